@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark: FFT GFLOP/s (5 n log2 n) and HBM-roofline fraction of the
+plain FP32 path on the large workload, with parity against the FP64 oracle.
+
+One step = one forward transform of each of the three large synthetic
+complex64 inputs (seed 1, re/im ~ U[-1,1)): 1-D n = 2^24 (lifted to
+4096 x 4096, two passes), 2-D 4096 x 4096 (two passes), 3-D 256^3 (three
+axis passes).  Each input is 128 MiB, larger than the 126 MB L2, so no L2
+flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl moa|reference]
+Multi-GPU (torchrun, one rank per GPU): every rank runs its own replica of
+the step (the transforms are independent problems; there is no exchange),
+the time is the max over ranks and the value is the whole-job throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FFT GFLOP/s (5n·log2n) & HBM-roofline fraction vs plain FP32 at rel-L2≤2e-6"
+WORKLOAD = [("1d_2^24", (1 << 24,)), ("2d_4096^2", (4096, 4096)), ("3d_256^3", (256, 256, 256))]
+WORKLOAD_NAME = ("complex64 forward FFT step: 1-D n=2^24 (r=c=4096 four-step) + 2-D 4096x4096 + 3-D 256^3, "
+                 "seed 1, re/im ~ U[-1,1)")
+TOL = 2e-6
+
+
+def numel(shape):
+    n = 1
+    for s in shape:
+        n *= s
+    return n
+
+
+def flops(shape):
+    n = numel(shape)
+    return 5.0 * n * math.log2(n)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_0811_2535_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)
+        ent = t.get("kernels", {}).get(kernel_key)
+        if ent and t.get("csrc_hash") == csrc_hash():
+            return float(ent["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled in the background."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        loaded = [s for s in sm if smax and s > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_step(shapes, seed):
+    """Run the FP64 oracle on the given shapes; returns (seconds, outputs)."""
+    import numpy as np
+
+    import oracle
+    from paper_0811_2535_gb300 import inputs
+    oracle.build()
+    outs, secs = [], 0.0
+    for shape in shapes:
+        x = inputs.uniform(shape, seed).astype(np.complex128)
+        t0 = time.perf_counter()
+        y = oracle.fft_radix2(x, -1) if len(shape) == 1 else oracle.fft_nd(x, len(shape), -1)
+        secs += time.perf_counter() - t0
+        outs.append(y)
+    return secs, outs
+
+
+def reference_shapes(scale_log2: int):
+    """The large workload with every transform shrunk by 2^scale_log2."""
+    s = scale_log2
+    return [(1 << (24 - s),), (4096, 4096 >> s), (256, 256, 256 >> s)]
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    from paper_0811_2535_gb300 import inputs
+    # pick the sample so that (warmup + steps) oracle steps take about 2 minutes
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    scale = 10
+    probe, _ = oracle_step(reference_shapes(scale), inputs.SEED_LARGE)
+    while scale > 0 and probe * 2.2 <= budget:
+        scale -= 1
+        probe *= 2.1
+    shapes = reference_shapes(scale)
+    for _ in range(args.warmup):
+        oracle_step(shapes, inputs.SEED_LARGE)
+    secs = 0.0
+    for _ in range(args.steps):
+        s, _ = oracle_step(shapes, inputs.SEED_LARGE)
+        secs += s
+    f = sum(flops(sh) for sh in shapes)
+    value = f * args.steps / secs / 1e9
+    sample = f"each step: 1-D 2^{24 - scale} + 2-D 4096x{4096 >> scale} + 3-D 256x256x{256 >> scale}, FP64 oracle"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "sample_scale_log2": scale},
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+# kernel launched by each pass of each workload (template name as ncu lists it)
+PASS_KERNELS = {
+    "1d_2^24": ["col_pass_kernel<12,true>", "row_pass_kernel<12>"],
+    "2d_4096^2": ["row_pass_kernel<12>", "col_pass_kernel<12,false>"],
+    "3d_256^3": ["row_pass_kernel<8>", "col_pass_kernel<8,false>", "col_pass_kernel<8,false>"],
+}
+
+
+def run_moa(args):
+    import numpy as np
+    import torch
+
+    from paper_0811_2535_gb300 import build as _build
+    from paper_0811_2535_gb300 import inputs, moafft
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    _build.build()
+    moafft.lib()
+
+    plans, xs, outs = [], [], []
+    for name, shape in WORKLOAD:
+        p = moafft.Plan(list(shape), 1, -1)
+        info = p.info()
+        assert info["passes"] == len(PASS_KERNELS[name]), (name, info)
+        plans.append(p)
+        xs.append(torch.from_numpy(inputs.uniform(shape, inputs.SEED_LARGE)).to(dev))
+        outs.append(torch.empty(numel(shape), dtype=torch.complex64, device=dev))
+    stream = torch.cuda.current_stream(dev)
+    npass = [len(PASS_KERNELS[name]) for name, _ in WORKLOAD]
+    launches_per_step = sum(npass)
+
+    def step(events=None, ei=0):
+        for p, x, o, k in zip(plans, xs, outs, npass):
+            for i in range(k):
+                p.exec_pass(i, x, o, stream=stream)
+                if events is not None:
+                    events[ei].record(stream)
+                    ei += 1
+        return ei
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # parity of the timed configuration (outputs of the last warm-up step)
+    parity = {}
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_oracle:
+        secs, refs = oracle_step([s for _, s in WORKLOAD], inputs.SEED_LARGE)
+        f = sum(flops(s) for _, s in WORKLOAD)
+        cpu_baseline = {"value": f / secs / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                        "sample": "one full step (1-D 2^24 + 2-D 4096^2 + 3-D 256^3), FP64, 1 thread"}
+        for (name, shape), o, ref in zip(WORKLOAD, outs, refs):
+            y = o.cpu().numpy().astype(np.complex128).reshape(-1)
+            r = ref.reshape(-1)
+            parity[name] = float(np.linalg.norm(y - r) / np.linalg.norm(r))
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    # a short untimed ramp so the sampler sees the clocks under load
+    for _ in range(max(3, args.warmup)):
+        step()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps * launches_per_step + 1)]
+    events[0].record(stream)
+    ei = 1
+    for _ in range(args.steps):
+        ei = step(events, ei)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+
+    total_ms = events[0].elapsed_time(events[-1])
+    per_kernel = {}
+    k = 0
+    for _ in range(args.steps):
+        for name, _shape in WORKLOAD:
+            for kname in PASS_KERNELS[name]:
+                per_kernel.setdefault((name, kname), []).append(events[k].elapsed_time(events[k + 1]))
+                k += 1
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    f_step = sum(flops(s) for _, s in WORKLOAD)
+    value = world * f_step * args.steps / (total_ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (largest share of the step time)
+    by_kernel = {}
+    for (name, kname), ds in per_kernel.items():
+        by_kernel.setdefault(kname, []).extend(ds)
+    dom = max(by_kernel, key=lambda kn: sum(by_kernel[kn]))
+    avg_ms = statistics.mean(by_kernel[dom])
+    bytes_per_launch = 16.0 * (1 << 24)     # read + write of n = 2^24 complex64 per pass
+    peak, peak_src = load_peaks()
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": load_traffic(dom), "kernel": dom, "peak_source": peak_src,
+                "share": sum(by_kernel[dom]) / sum(sum(v) for v in by_kernel.values())}
+    kernels = {f"{name}:{kname}": {"avg_us": statistics.mean(ds) * 1e3,
+                                   "GB_per_s": bytes_per_launch / (statistics.mean(ds) * 1e-3) / 1e9}
+               for (name, kname), ds in per_kernel.items()}
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e_steps = max(1, min(args.steps, 10))
+    hin = [torch.from_numpy(inputs.uniform(s, inputs.SEED_LARGE).reshape(-1)).pin_memory() for _, s in WORKLOAD]
+    hout = [torch.empty_like(h).pin_memory() for h in hin]
+    dbuf = [torch.empty(numel(s), dtype=torch.complex64, device=dev) for _, s in WORKLOAD]
+    for p, a, b, d in zip(plans, hin, hout, dbuf):
+        p.exec_host(a, b, d, stream=stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        for p, a, b, d in zip(plans, hin, hout, dbuf):
+            p.exec_host(a, b, d, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    e2e_ms = float(t.item())
+    io_bytes = sum(8 * numel(s) for _, s in WORKLOAD)
+    e2e = {"value": world * f_step * e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+           "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes}
+
+    for p in plans:
+        if p.status() != 0:
+            raise RuntimeError("device status word set after the benchmark")
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD_NAME, "l2": "inputs larger than L2 (128 MiB each), no flush",
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "passes_per_step": launches_per_step},
+                "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": launches_per_step * args.steps, "rel_l2": parity or None,
+                "parity_ok": (all(v <= TOL for v in parity.values()) if parity else None), "kernels": kernels}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["moa", "reference"], default="moa")
+    ap.add_argument("--no-oracle", action="store_true", help="skip the CPU oracle parity/baseline leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_moa(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,142 @@
+/*
+ * moa_fft.h -- C ABI of the GB300 MoA reshape-transpose FFT library
+ * (libmoafft.so).
+ *
+ * Problem statement (Hunt, Mullin, Rosenkrantz, Raynolds, "A
+ * transformation-based approach for the design of parallel/distributed
+ * scientific software: the FFT", Fig. 2.1): input x in C^n with n = 2^t,
+ * t >= 1; output the FFT of x.  This library computes, for exponent sign s,
+ *
+ *     X[k] = sum_{j=0}^{n-1} x[j] * exp(s * 2*pi*i * j*k / n),
+ *
+ * unnormalised in both directions (forward then inverse multiplies by n).
+ * The multi-dimensional transform is the 1-D transform applied along every
+ * axis (the Omega operator, Appendix B, Eq. B.6) of a row-major array (the
+ * gamma ordering, Appendix A, Definition A.1); the last axis is contiguous
+ * and the batch index is outermost.  Large 1-D sizes use the paper's
+ * dimension lifting n = r*c (Sec. 4.2-4.8, Fig. 4.9): r-point column
+ * transforms, twiddle, c-point row transforms, transposed store.
+ *
+ * Data: complex64, i.e. interleaved (re, im) IEEE binary32 pairs.
+ *
+ * Ownership and memory:
+ *   - A plan is an opaque handle owned by the library.  It owns its twiddle
+ *     tables, its workspace and its device status word; moa_fft_destroy
+ *     frees them.  Plans are not thread-safe: one host thread at a time may
+ *     use a plan.
+ *   - `in` and `out` are caller-owned DEVICE pointers, 8-byte aligned
+ *     (16-byte recommended), each holding at least batch * prod(n) complex64
+ *     values (for a batched-uneven plan: sum(lengths)).  in == out
+ *     (in-place) is allowed; any other overlap is undefined.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Execution is asynchronous on that stream: exec never
+ *     synchronises, never allocates and may be captured in a CUDA graph.
+ *
+ * Errors: every entry point returns a moa_status_t.  Argument checks happen
+ * on the host before any CUDA call, so they work without a GPU.  A kernel
+ * that detects a fault on the device records it in the plan's status word;
+ * read it with moa_fft_status after synchronising the stream.
+ */
+#ifndef MOA_FFT_H
+#define MOA_FFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MOA_API __attribute__((visibility("default")))
+#else
+#define MOA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct moa_fft_plan_s *moa_fft_plan_t;
+
+typedef enum {
+    MOA_C64 = 0,          /* plain FP32 complex64 arithmetic */
+    MOA_C64_TC_FP16 = 1,  /* complex64 I/O, radix-16 DFT blocks on FP16 tensor cores (hi/lo split) */
+    MOA_C64_TC_BF16 = 2   /* complex64 I/O, radix-16 DFT blocks on BF16 tensor cores (hi/lo split) */
+} moa_dtype_t;
+
+typedef enum {
+    MOA_OK = 0,
+    MOA_ERR_INVALID_ARG = 1,   /* NULL pointer, bad sign/dims/batch, dead plan handle */
+    MOA_ERR_INVALID_SIZE = 2,  /* a length that is not a power of two >= 2 */
+    MOA_ERR_UNSUPPORTED = 3,   /* valid request this build does not implement */
+    MOA_ERR_ALLOC = 4,         /* device or host allocation failed */
+    MOA_ERR_CUDA = 5,          /* a CUDA runtime call failed (no device, launch error) */
+    MOA_ERR_TIMEOUT = 6        /* a bounded device-side wait gave up */
+} moa_status_t;
+
+/* Create a plan for `batch` transforms of shape n[0..dims-1].
+ *   n      : dims lengths, each a power of two >= 2 (t >= 1, Fig. 2.1).
+ *            1-D: n[0] <= 2^24.  2-D/3-D: every n[i] <= 4096.
+ *   dims   : 1, 2 or 3.
+ *   batch  : >= 1; batch * prod(n) < 2^31.
+ *   sign   : -1 (forward, exp(-2 pi i jk/n)) or +1.
+ *   dtype  : a moa_dtype_t value.
+ * Builds the pass sequence, generates the twiddle tables in FP64 on the
+ * device (rounded once to FP32) and allocates the workspace; synchronises
+ * the device once.  On failure *plan is set to NULL. */
+MOA_API moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int64_t batch,
+                          int sign, int dtype);
+
+/* Create a plan for `count` independent 1-D transforms of uneven lengths
+ * lengths[0..count-1] (each a power of two in [2, 65536]).  Transform i
+ * reads and writes the contiguous block starting at element
+ * sum_{j<i} lengths[j] of `in` / `out`.  All transforms run in one
+ * persistent launch fed by a device work queue. */
+MOA_API moa_status_t moa_fft_plan_batched(moa_fft_plan_t *plan, const int64_t *lengths, int64_t count,
+                                  int sign, int dtype);
+
+/* Run the planned transform (sign as planned) from `in` to `out` on
+ * `stream`.  Asynchronous; no allocation; capturable. */
+MOA_API moa_status_t moa_fft_exec(moa_fft_plan_t plan, const void *in, void *out, void *stream);
+
+/* Run the adjoint of the planned transform: the unnormalised transform of
+ * the opposite sign (F^H = conj(F)^T = F with -sign), on the same plan. */
+MOA_API moa_status_t moa_fft_exec_adjoint(moa_fft_plan_t plan, const void *in, void *out, void *stream);
+
+/* Run only pass `index` (0 <= index < passes, see moa_fft_plan_info) of the
+ * planned transform with exponent sign `sign` (-1 or +1).  Running passes
+ * 0..passes-1 in order on one stream with the same (in, out) is exactly
+ * moa_fft_exec (sign = planned) or moa_fft_exec_adjoint (sign = -planned).
+ * Intended for instrumentation: it lets a caller time each kernel launch
+ * with CUDA events on its own stream. */
+MOA_API moa_status_t moa_fft_exec_pass(moa_fft_plan_t plan, int index, int sign, const void *in, void *out,
+                                       void *stream);
+
+/* End-to-end call for host data: copies `host_in` (pinned host memory
+ * recommended) to the caller's device buffer `dev_buf`, runs the transform
+ * in place there and copies the result to `host_out`, all on `stream`.
+ * Returns after enqueueing; synchronise the stream before reading
+ * host_out. */
+MOA_API moa_status_t moa_fft_exec_host(moa_fft_plan_t plan, const void *host_in, void *host_out,
+                               void *dev_buf, void *stream);
+
+/* Device status word of the plan (MOA_OK or the first error a kernel
+ * recorded), read with a synchronous copy; the word is then reset to
+ * MOA_OK. */
+MOA_API moa_status_t moa_fft_status(moa_fft_plan_t plan);
+
+/* Static, NUL-terminated description of a status code. */
+MOA_API const char *moa_fft_error_string(moa_status_t status);
+
+/* Describe the plan: number of kernel passes per exec, the r x c split of a
+ * lifted 1-D transform (0 when none) and the workspace size in bytes. Any
+ * output pointer may be NULL. */
+MOA_API moa_status_t moa_fft_plan_info(moa_fft_plan_t plan, int *passes, int64_t *split_r,
+                               int64_t *split_c, size_t *workspace_bytes);
+
+/* Destroy a plan and free everything it owns.  NULL is a no-op (MOA_OK);
+ * a handle that is not a live plan returns MOA_ERR_INVALID_ARG. */
+MOA_API moa_status_t moa_fft_destroy(moa_fft_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOA_FFT_H */

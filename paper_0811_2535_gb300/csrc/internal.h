@@ -1,0 +1,55 @@
+// Internal interfaces between the plan (moa_fft.cu), the pass kernels
+// (pass_kernels.cu) and the twiddle generator (twiddle.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace moa {
+
+enum PassKind { PASS_ROW = 0, PASS_COL = 1 };
+
+enum PassFlags {
+    FLAG_CONJ_IN = 1,    // conjugate on load (sign +1 via conj(F_-(conj x)))
+    FLAG_CONJ_OUT = 2,   // conjugate on store
+    FLAG_TW4 = 4         // multiply column outputs by w_{N*C}^(k*i) (four-step twiddle)
+};
+
+// One kernel launch: N-point transforms (N = 2^logN <= 4096) along one axis.
+//  PASS_COL: view [O][N][C] (row-major), transform along the middle axis,
+//            F consecutive columns per tile, output in the same view.
+//  PASS_ROW: view [O][N], transform along contiguous rows, F rows per tile;
+//            output row o, index k goes to (o / Rt)*(N*Rt) + (o % Rt) + Rt*k
+//            (Rt = 1: natural order; Rt = r: the four-step transpose).
+struct PassDesc {
+    int kind;
+    int logN;
+    int64_t O;
+    int64_t C;      // PASS_COL only
+    int64_t Rt;     // PASS_ROW only
+    int logF;       // log2 of transforms per tile
+    int src, dst;   // buffer ids: 0 = user in, 1 = user out, 2 = workspace
+    int tw4;        // apply the four-step twiddle (PASS_COL)
+};
+
+struct TwiddleSet {
+    const float2 *stage[13];   // per logN: stage tables (Sched<logN> layout), or null
+    const float2 *lo, *hi;     // two-level table of w_n^e: lo[e & (2^h-1)] * hi[e >> h]
+    int h;
+};
+
+// Launch one pass.  `flags` carries FLAG_CONJ_*; FLAG_TW4 is derived from d.
+cudaError_t launch_pass(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw,
+                        int flags, cudaStream_t stream);
+// Shared memory bytes and threads per block of a pass.
+size_t pass_smem_bytes(const PassDesc &d);
+int pass_threads(const PassDesc &d);
+// One-time per-process kernel attribute set-up (dynamic shared memory).
+cudaError_t prepare_kernels();
+
+// Twiddle generation (FP64 on the device, rounded once to FP32).
+int stage_table_entries(int logN);
+cudaError_t generate_stage_table(float2 *dst, int logN, cudaStream_t stream);
+// w_n^e for e < 2^h (lo) and w_n^(e*2^h) for e < n/2^h (hi); sign -1.
+cudaError_t generate_two_level(float2 *lo, float2 *hi, int logn, int h, cudaStream_t stream);
+
+}  // namespace moa

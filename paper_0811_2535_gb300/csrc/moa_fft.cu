@@ -1,0 +1,472 @@
+// Plan construction and the C ABI (include/moa_fft.h).
+//
+// A plan turns the problem statement of Fig. 2.1 (x in C^n, n = 2^t) into a
+// short sequence of kernel passes:
+//   * 1-D, n <= 4096: one row pass, the whole transform in one tile
+//     (the sequential loop of Sec. 3.6 held on chip).
+//   * 1-D, n > 4096: dimension lifting n = r*c (Sec. 4.2-4.8, Fig. 4.9):
+//     a column pass of r-point transforms with the twiddle w_n^(j2*k1)
+//     (block phase), then a row pass of c-point transforms whose store
+//     performs the transpose X[k1 + r*k2] (cyclic phase).  Any r*c split
+//     is correct (Sec. 4.8); the default is r = 2^floor(t/2).
+//   * 2-D / 3-D: the 1-D transform applied along every axis (Omega,
+//     Appendix B, Eq. B.6): a row pass on the last axis, column passes on
+//     the others.
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <set>
+#include <vector>
+
+#include "../../include/moa_fft.h"
+#include "internal.h"
+
+using moa::PassDesc;
+
+struct moa_fft_plan_s {
+    int dims = 0;
+    int64_t n[3] = {0, 0, 0};
+    int64_t batch = 0;
+    int sign = -1;
+    int dtype = 0;
+    int64_t total = 0;            // complex elements per exec
+    int64_t split_r = 0, split_c = 0;
+    std::vector<PassDesc> passes;
+    moa::TwiddleSet tw{};
+    void *dev_block = nullptr;    // twiddle tables + status word
+    float2 *workspace = nullptr;
+    size_t workspace_bytes = 0;
+    int *d_status = nullptr;
+};
+
+namespace {
+
+std::mutex g_plans_mu;
+std::set<moa_fft_plan_s *> g_plans;
+
+bool is_live(moa_fft_plan_s *p)
+{
+    std::lock_guard<std::mutex> lk(g_plans_mu);
+    return p && g_plans.count(p) != 0;
+}
+
+bool pow2_ge2(int64_t v) { return v >= 2 && (v & (v - 1)) == 0; }
+
+int ilog2(int64_t v)
+{
+    int l = 0;
+    while ((int64_t(1) << l) < v)
+        ++l;
+    return l;
+}
+
+int env_int(const char *name, int fallback)
+{
+    const char *s = std::getenv(name);
+    return (s && *s) ? std::atoi(s) : fallback;
+}
+
+// log2 of the tile size in complex elements (MOA_TILE_LOG2 overrides, 10..14)
+int tile_log2()
+{
+    int t = env_int("MOA_TILE_LOG2", 14);
+    return t < 10 ? 10 : (t > 14 ? 14 : t);
+}
+
+int threads_log2_per_transform(int logN) { return logN < 4 ? 0 : logN - 4; }
+
+int pick_logF_col(int logN, int64_t C)
+{
+    int lf = tile_log2() - logN;
+    const int lf_threads = 10 - threads_log2_per_transform(logN);
+    if (lf > lf_threads)
+        lf = lf_threads;
+    const int lc = ilog2(C);
+    if (lf > lc)
+        lf = lc;
+    return lf < 0 ? 0 : lf;
+}
+
+int pick_logF_row(int logN, int64_t O)
+{
+    int lf = tile_log2() - logN;
+    const int lf_threads = 10 - threads_log2_per_transform(logN);
+    if (lf > lf_threads)
+        lf = lf_threads;
+    int lo = 0;
+    while ((int64_t(1) << lo) < O)
+        ++lo;
+    if (lf > lo)
+        lf = lo;
+    return lf < 0 ? 0 : lf;
+}
+
+PassDesc row_pass(int logN, int64_t O, int64_t Rt, int src, int dst)
+{
+    PassDesc d{};
+    d.kind = moa::PASS_ROW;
+    d.logN = logN;
+    d.O = O;
+    d.C = 1;
+    d.Rt = Rt;
+    d.logF = pick_logF_row(logN, O);
+    d.src = src;
+    d.dst = dst;
+    d.tw4 = 0;
+    return d;
+}
+
+PassDesc col_pass(int logN, int64_t O, int64_t C, int tw4, int src, int dst)
+{
+    PassDesc d{};
+    d.kind = moa::PASS_COL;
+    d.logN = logN;
+    d.O = O;
+    d.C = C;
+    d.Rt = 1;
+    d.logF = pick_logF_col(logN, C);
+    d.src = src;
+    d.dst = dst;
+    d.tw4 = tw4;
+    return d;
+}
+
+enum { BUF_IN = 0, BUF_OUT = 1, BUF_WS = 2 };
+
+// Fault injection for host-side tests: MOA_FAULT_ALLOC=1 makes every plan
+// allocation fail before cudaMalloc is called.
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    if (env_int("MOA_FAULT_ALLOC", 0) == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+void free_plan_memory(moa_fft_plan_s *p)
+{
+    if (p->dev_block)
+        cudaFree(p->dev_block);
+    if (p->workspace)
+        cudaFree(p->workspace);
+    p->dev_block = nullptr;
+    p->workspace = nullptr;
+}
+
+moa_status_t build_passes(moa_fft_plan_s *p)
+{
+    const int64_t B = p->batch;
+    if (p->dims == 1) {
+        const int64_t n = p->n[0];
+        const int L = ilog2(n);
+        if (L <= 12) {
+            p->passes.push_back(row_pass(L, B, 1, BUF_IN, BUF_OUT));
+            return MOA_OK;
+        }
+        int lr = env_int("MOA_SPLIT_LOG2R", L / 2);
+        if (lr < 1 || lr > 12 || L - lr < 1 || L - lr > 12)
+            lr = L / 2;
+        const int lc = L - lr;
+        p->split_r = int64_t(1) << lr;
+        p->split_c = int64_t(1) << lc;
+        p->passes.push_back(col_pass(lr, B, p->split_c, 1, BUF_IN, BUF_WS));
+        p->passes.push_back(row_pass(lc, B * p->split_r, p->split_r, BUF_WS, BUF_OUT));
+        p->workspace_bytes = (size_t)p->total * sizeof(float2);
+        return MOA_OK;
+    }
+    // multi-D: last axis as rows, then every other axis as columns, in place
+    const int d = p->dims;
+    int src = BUF_IN;
+    p->passes.push_back(row_pass(ilog2(p->n[d - 1]), p->total / p->n[d - 1], 1, src, BUF_OUT));
+    for (int a = d - 2; a >= 0; --a) {
+        int64_t inner = 1, outer = B;
+        for (int k = a + 1; k < d; ++k)
+            inner *= p->n[k];
+        for (int k = 0; k < a; ++k)
+            outer *= p->n[k];
+        p->passes.push_back(col_pass(ilog2(p->n[a]), outer, inner, 0, BUF_OUT, BUF_OUT));
+    }
+    return MOA_OK;
+}
+
+moa_status_t allocate_and_fill(moa_fft_plan_s *p)
+{
+    // layout of the device block: status word, stage tables, two-level tables
+    bool need_stage[13] = {false};
+    for (const PassDesc &d : p->passes)
+        need_stage[d.logN] = true;
+    size_t offs[13] = {0};
+    size_t bytes = 256;  // status word
+    for (int l = 1; l <= 12; ++l) {
+        if (!need_stage[l])
+            continue;
+        const int ent = moa::stage_table_entries(l);
+        if (ent > 0) {
+            offs[l] = bytes;
+            bytes += ((size_t)ent * sizeof(float2) + 255) & ~size_t(255);
+        }
+    }
+    size_t lo_off = 0, hi_off = 0;
+    int logn = 0, h = 0;
+    if (p->split_r > 0) {
+        logn = ilog2(p->total / p->batch);
+        h = (logn + 1) / 2;
+        lo_off = bytes;
+        bytes += ((size_t(1) << h) * sizeof(float2) + 255) & ~size_t(255);
+        hi_off = bytes;
+        bytes += ((size_t(1) << (logn - h)) * sizeof(float2) + 255) & ~size_t(255);
+    }
+    void *blk = nullptr;
+    if (dev_alloc(&blk, bytes) != cudaSuccess)
+        return MOA_ERR_ALLOC;
+    p->dev_block = blk;
+    if (p->workspace_bytes) {
+        void *ws = nullptr;
+        if (dev_alloc(&ws, p->workspace_bytes) != cudaSuccess)
+            return MOA_ERR_ALLOC;
+        p->workspace = static_cast<float2 *>(ws);
+    }
+    char *base = static_cast<char *>(blk);
+    p->d_status = reinterpret_cast<int *>(base);
+    if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess)
+        return MOA_ERR_CUDA;
+    if (moa::prepare_kernels() != cudaSuccess)
+        return MOA_ERR_CUDA;
+    for (int l = 1; l <= 12; ++l) {
+        p->tw.stage[l] = nullptr;
+        if (offs[l]) {
+            p->tw.stage[l] = reinterpret_cast<float2 *>(base + offs[l]);
+            if (moa::generate_stage_table(const_cast<float2 *>(p->tw.stage[l]), l, 0) != cudaSuccess)
+                return MOA_ERR_CUDA;
+        }
+    }
+    if (p->split_r > 0) {
+        float2 *lo = reinterpret_cast<float2 *>(base + lo_off);
+        float2 *hi = reinterpret_cast<float2 *>(base + hi_off);
+        if (moa::generate_two_level(lo, hi, logn, h, 0) != cudaSuccess)
+            return MOA_ERR_CUDA;
+        p->tw.lo = lo;
+        p->tw.hi = hi;
+        p->tw.h = h;
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess)
+        return MOA_ERR_CUDA;
+    return MOA_OK;
+}
+
+moa_status_t check_io(const void *in, const void *out)
+{
+    if (!in || !out || (reinterpret_cast<uintptr_t>(in) & 7) || (reinterpret_cast<uintptr_t>(out) & 7))
+        return MOA_ERR_INVALID_ARG;
+    return MOA_OK;
+}
+
+moa_status_t run_pass(moa_fft_plan_s *p, size_t i, const void *in, void *out, cudaStream_t s, int sign)
+{
+    const PassDesc &d = p->passes[i];
+    const size_t np = p->passes.size();
+    auto buf = [&](int id) -> float2 * {
+        return id == BUF_IN ? const_cast<float2 *>(static_cast<const float2 *>(in))
+                            : (id == BUF_OUT ? static_cast<float2 *>(out) : p->workspace);
+    };
+    // sign +1 is conj(F_-(conj x)): conjugate on the first load and last store
+    int flags = 0;
+    if (sign > 0) {
+        if (i == 0)
+            flags |= moa::FLAG_CONJ_IN;
+        if (i + 1 == np)
+            flags |= moa::FLAG_CONJ_OUT;
+    }
+    if (moa::launch_pass(d, buf(d.src), buf(d.dst), p->tw, flags, s) != cudaSuccess)
+        return MOA_ERR_CUDA;
+    return MOA_OK;
+}
+
+moa_status_t run(moa_fft_plan_s *p, const void *in, void *out, void *stream, int sign)
+{
+    if (!is_live(p))
+        return MOA_ERR_INVALID_ARG;
+    moa_status_t st = check_io(in, out);
+    if (st != MOA_OK)
+        return st;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (size_t i = 0; i < p->passes.size(); ++i)
+        if ((st = run_pass(p, i, in, out, s, sign)) != MOA_OK)
+            return st;
+    return MOA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int64_t batch, int sign, int dtype)
+{
+    if (!plan)
+        return MOA_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if (!n || dims < 1 || dims > 3 || batch < 1 || (sign != 1 && sign != -1))
+        return MOA_ERR_INVALID_ARG;
+    if (dtype != MOA_C64 && dtype != MOA_C64_TC_FP16 && dtype != MOA_C64_TC_BF16)
+        return MOA_ERR_INVALID_ARG;
+    int64_t total = batch;
+    for (int i = 0; i < dims; ++i) {
+        if (!pow2_ge2(n[i]))
+            return MOA_ERR_INVALID_SIZE;
+        if (dims == 1 ? n[i] > (int64_t(1) << 24) : n[i] > 4096)
+            return MOA_ERR_UNSUPPORTED;
+        total *= n[i];
+        if (total >= (int64_t(1) << 31))
+            return MOA_ERR_UNSUPPORTED;
+    }
+    if (dtype != MOA_C64)
+        return MOA_ERR_UNSUPPORTED;
+
+    moa_fft_plan_s *p = new (std::nothrow) moa_fft_plan_s();
+    if (!p)
+        return MOA_ERR_ALLOC;
+    p->dims = dims;
+    for (int i = 0; i < dims; ++i)
+        p->n[i] = n[i];
+    p->batch = batch;
+    p->sign = sign;
+    p->dtype = dtype;
+    p->total = total;
+    moa_status_t st = build_passes(p);
+    if (st == MOA_OK)
+        st = allocate_and_fill(p);
+    if (st != MOA_OK) {
+        free_plan_memory(p);
+        delete p;
+        return st;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_plans_mu);
+        g_plans.insert(p);
+    }
+    *plan = p;
+    return MOA_OK;
+}
+
+moa_status_t moa_fft_plan_batched(moa_fft_plan_t *plan, const int64_t *lengths, int64_t count, int sign,
+                                  int dtype)
+{
+    if (!plan)
+        return MOA_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if (!lengths || count < 1 || (sign != 1 && sign != -1))
+        return MOA_ERR_INVALID_ARG;
+    if (dtype != MOA_C64 && dtype != MOA_C64_TC_FP16 && dtype != MOA_C64_TC_BF16)
+        return MOA_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < count; ++i)
+        if (!pow2_ge2(lengths[i]))
+            return MOA_ERR_INVALID_SIZE;
+    return MOA_ERR_UNSUPPORTED;
+}
+
+moa_status_t moa_fft_exec(moa_fft_plan_t plan, const void *in, void *out, void *stream)
+{
+    if (!is_live(plan))
+        return MOA_ERR_INVALID_ARG;
+    return run(plan, in, out, stream, plan->sign);
+}
+
+moa_status_t moa_fft_exec_adjoint(moa_fft_plan_t plan, const void *in, void *out, void *stream)
+{
+    if (!is_live(plan))
+        return MOA_ERR_INVALID_ARG;
+    return run(plan, in, out, stream, -plan->sign);
+}
+
+moa_status_t moa_fft_exec_pass(moa_fft_plan_t plan, int index, int sign, const void *in, void *out,
+                               void *stream)
+{
+    if (!is_live(plan) || (sign != 1 && sign != -1))
+        return MOA_ERR_INVALID_ARG;
+    if (index < 0 || (size_t)index >= plan->passes.size())
+        return MOA_ERR_INVALID_ARG;
+    moa_status_t st = check_io(in, out);
+    if (st != MOA_OK)
+        return st;
+    return run_pass(plan, (size_t)index, in, out, static_cast<cudaStream_t>(stream), sign);
+}
+
+moa_status_t moa_fft_exec_host(moa_fft_plan_t plan, const void *host_in, void *host_out, void *dev_buf,
+                               void *stream)
+{
+    if (!is_live(plan))
+        return MOA_ERR_INVALID_ARG;
+    if (!host_in || !host_out || !dev_buf)
+        return MOA_ERR_INVALID_ARG;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)plan->total * sizeof(float2);
+    if (cudaMemcpyAsync(dev_buf, host_in, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return MOA_ERR_CUDA;
+    moa_status_t st = run(plan, dev_buf, dev_buf, stream, plan->sign);
+    if (st != MOA_OK)
+        return st;
+    if (cudaMemcpyAsync(host_out, dev_buf, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return MOA_ERR_CUDA;
+    return MOA_OK;
+}
+
+moa_status_t moa_fft_status(moa_fft_plan_t plan)
+{
+    if (!is_live(plan))
+        return MOA_ERR_INVALID_ARG;
+    int h = 0;
+    if (cudaMemcpy(&h, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return MOA_ERR_CUDA;
+    if (h != 0 && cudaMemset(plan->d_status, 0, sizeof(int)) != cudaSuccess)
+        return MOA_ERR_CUDA;
+    return static_cast<moa_status_t>(h);
+}
+
+const char *moa_fft_error_string(moa_status_t status)
+{
+    switch (status) {
+    case MOA_OK: return "success";
+    case MOA_ERR_INVALID_ARG: return "invalid argument";
+    case MOA_ERR_INVALID_SIZE: return "invalid size (lengths must be powers of two >= 2)";
+    case MOA_ERR_UNSUPPORTED: return "unsupported configuration";
+    case MOA_ERR_ALLOC: return "allocation failed";
+    case MOA_ERR_CUDA: return "CUDA runtime error";
+    case MOA_ERR_TIMEOUT: return "device-side wait timed out";
+    default: return "unknown status";
+    }
+}
+
+moa_status_t moa_fft_plan_info(moa_fft_plan_t plan, int *passes, int64_t *split_r, int64_t *split_c,
+                               size_t *workspace_bytes)
+{
+    if (!is_live(plan))
+        return MOA_ERR_INVALID_ARG;
+    if (passes)
+        *passes = (int)plan->passes.size();
+    if (split_r)
+        *split_r = plan->split_r;
+    if (split_c)
+        *split_c = plan->split_c;
+    if (workspace_bytes)
+        *workspace_bytes = plan->workspace_bytes;
+    return MOA_OK;
+}
+
+moa_status_t moa_fft_destroy(moa_fft_plan_t plan)
+{
+    if (!plan)
+        return MOA_OK;
+    {
+        std::lock_guard<std::mutex> lk(g_plans_mu);
+        if (!g_plans.erase(plan))
+            return MOA_ERR_INVALID_ARG;
+    }
+    free_plan_memory(plan);
+    delete plan;
+    return MOA_OK;
+}
+
+}  // extern "C"

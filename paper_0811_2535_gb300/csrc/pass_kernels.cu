@@ -1,0 +1,228 @@
+// Pass kernels: the column pass (strided axis, paper's block phase with the
+// four-step twiddle in its epilogue) and the row pass (contiguous axis,
+// paper's cyclic phase with the transposed store).  See internal.h for the
+// views each pass works on.
+//
+// Tiles: F transforms of length N per thread block (F*N <= 2^14 complex64,
+// 128 KiB), one thread per 16 points.  Loads and stores go straight between
+// HBM and registers: in the column pass the F lanes that share a row read
+// or write F*8 contiguous bytes (F >= 4 gives whole 32-byte sectors); in the
+// row pass the F lanes that share a column index write the F outputs of the
+// four-step transpose X[k1 + r*k2] next to each other.
+#include "fft_core.cuh"
+#include "internal.h"
+
+namespace moa {
+
+namespace {
+
+__device__ __forceinline__ float2 two_level(const float2 *__restrict__ lo, const float2 *__restrict__ hi,
+                                            int h, int64_t e)
+{
+    return cmul(__ldg(&lo[e & ((int64_t(1) << h) - 1)]), __ldg(&hi[e >> h]));
+}
+
+template <int LOGN, bool TW4>
+__global__ void __launch_bounds__(1024) col_pass_kernel(const float2 *in, float2 *out, int C, int logF,
+                                                        int logTpo, const float2 *__restrict__ tw,
+                                                        const float2 *__restrict__ tw_lo,
+                                                        const float2 *__restrict__ tw_hi, int tw_h, int flags)
+{
+    using Sc = Sched<LOGN>;
+    extern __shared__ float2 smem[];
+    const int F = 1 << logF;
+    const int tid = threadIdx.x;
+    const int f = tid & (F - 1);
+    const int tau = tid >> logF;
+    const unsigned tile = blockIdx.x;
+    const unsigned o = tile >> logTpo;
+    const int col = (int)((tile & ((1u << logTpo) - 1)) << logF) + f;
+    // N*C < 2^31 (checked at plan time), so in-column offsets fit in 32 bits
+    const int64_t base = (int64_t)o * ((int64_t)Sc::N * C) + col + (int64_t)tau * C;
+    const int step = Sc::T * C;
+
+    float2 v[16];
+    {
+        constexpr int R0 = 1 << Sc::rlog(0);
+        constexpr int NB0 = Sc::P / R0;
+        const float2 *src = in + base;
+        // element tau + T*q lands in register (q % NB0)*R0 + q / NB0
+#pragma unroll
+        for (int q = 0; q < Sc::P; ++q)
+            v[(q % NB0) * R0 + q / NB0] = src[q * step];
+    }
+    if (flags & FLAG_CONJ_IN) {
+#pragma unroll
+        for (int r = 0; r < Sc::P; ++r)
+            v[r].y = -v[r].y;
+    }
+
+    constexpr int kExchange = Sc::S > 1 ? (Sc::N + Sc::N / 16) : 0;
+    float2 *tk = smem + (kExchange << logF);
+    (void)tk;
+    if constexpr (TW4) {
+        // w_n^(col*k1), k1 = tau + T*k, as A * Tk[k]: A = w_n^(col*tau) per
+        // thread, Tk[k] = w_n^(col*T*k) shared by the lanes of one column.
+        for (int k = tau; k < Sc::P; k += Sc::T)
+            tk[(k << logF) + f] = two_level(tw_lo, tw_hi, tw_h, (int64_t)col * (Sc::T * k));
+    }
+
+    fft_tile<LOGN>(v, smem, tau, f, logF, tw);
+
+    if constexpr (TW4) {
+        const float2 A = two_level(tw_lo, tw_hi, tw_h, (int64_t)col * tau);
+        if constexpr (Sc::S == 1)
+            __syncthreads();
+#pragma unroll
+        for (int k = 0; k < Sc::P; ++k)
+            v[k] = cmul(v[k], cmul(A, tk[(k << logF) + f]));
+    }
+    if (flags & FLAG_CONJ_OUT) {
+#pragma unroll
+        for (int k = 0; k < Sc::P; ++k)
+            v[k].y = -v[k].y;
+    }
+    float2 *dst = out + base;
+#pragma unroll
+    for (int k = 0; k < Sc::P; ++k)
+        dst[k * step] = v[k];
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(1024) row_pass_kernel(const float2 *in, float2 *out, int64_t O, int64_t Rt,
+                                                        int logF, const float2 *__restrict__ tw, int flags)
+{
+    using Sc = Sched<LOGN>;
+    extern __shared__ float2 smem[];
+    const int F = 1 << logF;
+    const int tid = threadIdx.x;
+    const int f = tid & (F - 1);
+    const int tau = tid >> logF;
+    const int64_t o = ((int64_t)blockIdx.x << logF) + f;
+    const bool active = o < O;
+
+    float2 v[16];
+    if (active) {
+        const float2 *src = in + o * Sc::N;
+#pragma unroll
+        for (int r = 0; r < Sc::P; ++r)
+            v[r] = src[load_index<LOGN>(r, tau)];
+    } else {
+#pragma unroll
+        for (int r = 0; r < Sc::P; ++r)
+            v[r] = make_float2(0.f, 0.f);
+    }
+    if (flags & FLAG_CONJ_IN) {
+#pragma unroll
+        for (int r = 0; r < Sc::P; ++r)
+            v[r].y = -v[r].y;
+    }
+
+    fft_tile<LOGN>(v, smem, tau, f, logF, tw);
+
+    if (flags & FLAG_CONJ_OUT) {
+#pragma unroll
+        for (int k = 0; k < Sc::P; ++k)
+            v[k].y = -v[k].y;
+    }
+    if (active) {
+        const int64_t ob = o / Rt, orow = o - ob * Rt;
+        float2 *dst = out + ob * (Sc::N * Rt) + orow;
+#pragma unroll
+        for (int k = 0; k < Sc::P; ++k)
+            dst[(int64_t)(tau + Sc::T * k) * Rt] = v[k];
+    }
+}
+
+template <int LOGN>
+cudaError_t launch_typed(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
+                         cudaStream_t stream)
+{
+    const int threads = pass_threads(d);
+    const size_t smem = pass_smem_bytes(d);
+    if (d.kind == PASS_COL) {
+        int logTpo = 0;
+        while ((int64_t(1) << logTpo) < (d.C >> d.logF))
+            ++logTpo;
+        const int64_t grid = d.O << logTpo;
+        if (d.tw4)
+            col_pass_kernel<LOGN, true><<<(unsigned)grid, threads, smem, stream>>>(
+                in, out, (int)d.C, d.logF, logTpo, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags);
+        else
+            col_pass_kernel<LOGN, false><<<(unsigned)grid, threads, smem, stream>>>(
+                in, out, (int)d.C, d.logF, logTpo, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags);
+    } else {
+        const int64_t grid = (d.O + (int64_t(1) << d.logF) - 1) >> d.logF;
+        row_pass_kernel<LOGN><<<(unsigned)grid, threads, smem, stream>>>(in, out, d.O, d.Rt, d.logF,
+                                                                         tw.stage[LOGN], flags);
+    }
+    return cudaGetLastError();
+}
+
+template <int LOGN>
+cudaError_t set_attrs()
+{
+    const int max_smem = 227 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(col_pass_kernel<LOGN, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaFuncSetAttribute(col_pass_kernel<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(row_pass_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+}
+
+}  // namespace
+
+int pass_threads(const PassDesc &d)
+{
+    const int N = 1 << d.logN;
+    const int T = N < 16 ? 1 : N / 16;
+    return T << d.logF;
+}
+
+size_t pass_smem_bytes(const PassDesc &d)
+{
+    const int N = 1 << d.logN;
+    const int P = N < 16 ? N : 16;
+    const size_t F = size_t(1) << d.logF;
+    size_t entries = 0;
+    if (d.logN > 4)
+        entries += (size_t)(N + N / 16) * F;
+    if (d.kind == PASS_COL && d.tw4)
+        entries += (size_t)P * F;
+    return entries * sizeof(float2);
+}
+
+cudaError_t prepare_kernels()
+{
+    cudaError_t e = cudaSuccess;
+    if ((e = set_attrs<1>()) || (e = set_attrs<2>()) || (e = set_attrs<3>()) || (e = set_attrs<4>()) ||
+        (e = set_attrs<5>()) || (e = set_attrs<6>()) || (e = set_attrs<7>()) || (e = set_attrs<8>()) ||
+        (e = set_attrs<9>()) || (e = set_attrs<10>()) || (e = set_attrs<11>()) || (e = set_attrs<12>()))
+        return e;
+    return cudaSuccess;
+}
+
+cudaError_t launch_pass(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
+                        cudaStream_t stream)
+{
+    switch (d.logN) {
+    case 1: return launch_typed<1>(d, in, out, tw, flags, stream);
+    case 2: return launch_typed<2>(d, in, out, tw, flags, stream);
+    case 3: return launch_typed<3>(d, in, out, tw, flags, stream);
+    case 4: return launch_typed<4>(d, in, out, tw, flags, stream);
+    case 5: return launch_typed<5>(d, in, out, tw, flags, stream);
+    case 6: return launch_typed<6>(d, in, out, tw, flags, stream);
+    case 7: return launch_typed<7>(d, in, out, tw, flags, stream);
+    case 8: return launch_typed<8>(d, in, out, tw, flags, stream);
+    case 9: return launch_typed<9>(d, in, out, tw, flags, stream);
+    case 10: return launch_typed<10>(d, in, out, tw, flags, stream);
+    case 11: return launch_typed<11>(d, in, out, tw, flags, stream);
+    case 12: return launch_typed<12>(d, in, out, tw, flags, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace moa

@@ -1,0 +1,223 @@
+"""Python binding of libmoafft.so (the C ABI in include/moa_fft.h).
+
+Argument marshalling only: every transform runs in the library's CUDA
+kernels.  PyTorch supplies device memory (``tensor.data_ptr()``) and the
+stream (``torch.cuda.current_stream().cuda_stream``).  There is no CPU or
+library fallback: if the shared library is missing or cannot be loaded the
+first call raises.
+
+Conventions follow the C ABI: complex64, row-major, batch outermost,
+unnormalised, ``sign`` in {-1, +1} with X[k] = sum_j x[j] exp(sign 2 pi i jk/n).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmoafft.so")
+
+MOA_C64, MOA_C64_TC_FP16, MOA_C64_TC_BF16 = 0, 1, 2
+STATUS = {0: "MOA_OK", 1: "MOA_ERR_INVALID_ARG", 2: "MOA_ERR_INVALID_SIZE", 3: "MOA_ERR_UNSUPPORTED",
+          4: "MOA_ERR_ALLOC", 5: "MOA_ERR_CUDA", 6: "MOA_ERR_TIMEOUT"}
+
+# every symbol the header declares, with (restype, argtypes)
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+SIGNATURES = {
+    "moa_fft_plan": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.c_int, _I64,
+                                    ctypes.c_int, ctypes.c_int]),
+    "moa_fft_plan_batched": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_I64), _I64, ctypes.c_int,
+                                            ctypes.c_int]),
+    "moa_fft_exec": (ctypes.c_int, [_P, _P, _P, _P]),
+    "moa_fft_exec_adjoint": (ctypes.c_int, [_P, _P, _P, _P]),
+    "moa_fft_exec_pass": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+    "moa_fft_exec_host": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "moa_fft_status": (ctypes.c_int, [_P]),
+    "moa_fft_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "moa_fft_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64),
+                                         ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_size_t)]),
+    "moa_fft_destroy": (ctypes.c_int, [_P]),
+}
+
+_lib = None
+
+
+class MoaError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {STATUS.get(code, code)} ({error_string(code) if _lib else ''})")
+
+
+def lib() -> ctypes.CDLL:
+    """Load libmoafft.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libmoafft.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def error_string(code: int) -> str:
+    return lib().moa_fft_error_string(code).decode()
+
+
+def _check(code: int, what: str) -> None:
+    if code != 0:
+        raise MoaError(code, what)
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Plan:
+    """A plan for ``batch`` transforms of ``shape`` (1-, 2- or 3-D)."""
+
+    def __init__(self, shape: Sequence[int], batch: int = 1, sign: int = -1, dtype: int = MOA_C64):
+        shape = [int(s) for s in (shape if hasattr(shape, "__len__") else [shape])]
+        self.shape, self.batch, self.sign, self.dtype = tuple(shape), int(batch), int(sign), int(dtype)
+        arr = (_I64 * len(shape))(*shape)
+        h = _P()
+        _check(lib().moa_fft_plan(ctypes.byref(h), arr, len(shape), self.batch, self.sign, self.dtype),
+               f"moa_fft_plan{tuple(shape)}x{batch}")
+        self._h = h
+
+    @property
+    def numel(self) -> int:
+        n = self.batch
+        for s in self.shape:
+            n *= s
+        return n
+
+    def _io(self, x, out):
+        import torch
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.complex64):
+            raise TypeError("input must be a complex64 CUDA tensor")
+        if not x.is_contiguous():
+            x = x.contiguous()
+        if x.numel() != self.numel:
+            raise ValueError(f"input has {x.numel()} elements, plan expects {self.numel}")
+        if out is None:
+            out = torch.empty_like(x)
+        elif not (out.is_cuda and out.dtype == torch.complex64 and out.is_contiguous() and out.numel() == self.numel):
+            raise ValueError("out must be a contiguous complex64 CUDA tensor of the plan's size")
+        return x, out
+
+    def exec(self, x, out=None, stream=None):
+        """Transform ``x`` (complex64 CUDA tensor) into ``out`` (new if None)."""
+        x, out = self._io(x, out)
+        _check(lib().moa_fft_exec(self._h, x.data_ptr(), out.data_ptr(), _stream_ptr(stream)), "moa_fft_exec")
+        return out
+
+    def exec_adjoint(self, x, out=None, stream=None):
+        """Opposite-sign unnormalised transform (F^H) on the same plan."""
+        x, out = self._io(x, out)
+        _check(lib().moa_fft_exec_adjoint(self._h, x.data_ptr(), out.data_ptr(), _stream_ptr(stream)),
+               "moa_fft_exec_adjoint")
+        return out
+
+    def exec_pass(self, index: int, x, out, sign: Optional[int] = None, stream=None):
+        """Run only pass ``index`` (instrumentation: per-kernel timing)."""
+        s = self.sign if sign is None else int(sign)
+        _check(lib().moa_fft_exec_pass(self._h, int(index), s, x.data_ptr(), out.data_ptr(), _stream_ptr(stream)),
+               "moa_fft_exec_pass")
+        return out
+
+    def exec_host(self, host_in, host_out, dev_buf, stream=None):
+        """Host-memory round trip through ``dev_buf`` (all three torch tensors)."""
+        _check(lib().moa_fft_exec_host(self._h, host_in.data_ptr(), host_out.data_ptr(), dev_buf.data_ptr(),
+                                       _stream_ptr(stream)), "moa_fft_exec_host")
+        return host_out
+
+    def status(self) -> int:
+        return lib().moa_fft_status(self._h)
+
+    def info(self) -> dict:
+        p = ctypes.c_int()
+        r = _I64()
+        c = _I64()
+        w = ctypes.c_size_t()
+        _check(lib().moa_fft_plan_info(self._h, ctypes.byref(p), ctypes.byref(r), ctypes.byref(c), ctypes.byref(w)),
+               "moa_fft_plan_info")
+        return {"passes": p.value, "split_r": r.value, "split_c": c.value, "workspace_bytes": w.value}
+
+    def destroy(self) -> None:
+        if getattr(self, "_h", None):
+            lib().moa_fft_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+_plan_cache: dict = {}
+
+
+def _cached_plan(shape, batch, sign):
+    key = (tuple(shape), int(batch), int(sign))
+    p = _plan_cache.get(key)
+    if p is None:
+        p = Plan(shape, batch, sign)
+        _plan_cache[key] = p
+    return p
+
+
+def fft(x, dims: int = 1, sign: int = -1):
+    """Unnormalised DFT of ``x`` (complex64 CUDA tensor) over its last
+    ``dims`` axes; leading axes are the batch."""
+    shape = tuple(x.shape[x.dim() - dims:])
+    batch = 1
+    for s in x.shape[:x.dim() - dims]:
+        batch *= int(s)
+    return _cached_plan(shape, batch, sign).exec(x.contiguous()).view(x.shape)
+
+
+def _autograd():
+    import torch
+
+    class MoaFFTFunction(torch.autograd.Function):
+        """y = F x with F the plan's transform; the backward pass applies the
+        adjoint kernel.  For a linear map y = F x and a real loss L, PyTorch's
+        complex gradient convention gives grad_x = F^H grad_y, and F^H is the
+        opposite-sign unnormalised transform on the same plan, so nothing is
+        saved for the backward pass."""
+
+        @staticmethod
+        def forward(ctx, x, plan):
+            ctx.plan = plan
+            return plan.exec(x.contiguous()).view(x.shape)
+
+        @staticmethod
+        def backward(ctx, g):
+            return ctx.plan.exec_adjoint(g.contiguous()).view(g.shape), None
+
+    return MoaFFTFunction
+
+
+_MoaFFTFunction = None
+
+
+def MoaFFTFunction():
+    global _MoaFFTFunction
+    if _MoaFFTFunction is None:
+        _MoaFFTFunction = _autograd()
+    return _MoaFFTFunction
+
+
+def fft_autograd(x, plan: Plan):
+    """Differentiable transform: ``MoaFFTFunction.apply(x, plan)``."""
+    return MoaFFTFunction().apply(x, plan)

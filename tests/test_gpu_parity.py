@@ -1,0 +1,190 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64
+oracle on the same seeded complex64 inputs (promoted to FP64 for the
+oracle).  Tolerance: relative L2 error <= 2e-6 per transform, the bound the
+plain FP32 path must meet at every size."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-6
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0811_2535_gb300 import build, moafft
+    build.build()
+    import oracle
+    oracle.build()
+    return torch, moafft, oracle
+
+
+def per_transform_rel(y, ref, batch):
+    y = np.asarray(y, np.complex128).reshape(batch, -1)
+    ref = np.asarray(ref, np.complex128).reshape(batch, -1)
+    return np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+
+
+def run(env, shape, batch, sign, x, inplace=False, adjoint=False):
+    torch, moafft, _ = env
+    plan = moafft.Plan(shape, batch, sign)
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    if inplace:
+        out = plan.exec_adjoint(xd, out=xd) if adjoint else plan.exec(xd, out=xd)
+    else:
+        out = plan.exec_adjoint(xd) if adjoint else plan.exec(xd)
+    y = out.cpu().numpy()
+    assert plan.status() == 0
+    info = plan.info()
+    plan.destroy()
+    return y, info
+
+
+def oracle_ref(env, x, shape, batch, sign):
+    _, _, oracle = env
+    x64 = np.asarray(x, np.complex128).reshape((batch,) + tuple(shape))
+    if len(shape) == 1:
+        return oracle.fft_radix2(x64, sign)
+    return oracle.fft_nd(x64, len(shape), sign)
+
+
+@pytest.mark.parametrize("t", range(1, 25))
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_1d_every_size(env, t, sign):
+    from paper_0811_2535_gb300 import inputs
+    n = 1 << t
+    x = inputs.uniform(n, 1000 + t)
+    y, info = run(env, [n], 1, sign, x)
+    err = per_transform_rel(y, oracle_ref(env, x, [n], 1, sign), 1).max()
+    assert err <= TOL, (n, err)
+    assert info["passes"] == (1 if t <= 12 else 2)
+
+
+@pytest.mark.parametrize("n,batch", [(2, 3), (16, 5), (32, 7), (1024, 5), (4096, 3), (8192, 3), (1 << 16, 5),
+                                     (1 << 20, 2)])
+def test_1d_batched_ragged(env, n, batch):
+    from paper_0811_2535_gb300 import inputs
+    x = inputs.uniform((batch, n), 2000 + n + batch)
+    y, _ = run(env, [n], batch, -1, x)
+    err = per_transform_rel(y, oracle_ref(env, x, [n], batch, -1), batch)
+    assert err.max() <= TOL, err
+
+
+@pytest.mark.parametrize("t", [13, 14, 17, 20, 24])
+def test_1d_every_split(env, t, monkeypatch):
+    """Sec. 4.8: any breakpoint (here: any r x c split) gives the same result."""
+    from paper_0811_2535_gb300 import inputs
+    n = 1 << t
+    x = inputs.uniform(n, 3000 + t)
+    ref = oracle_ref(env, x, [n], 1, -1)
+    for lr in range(max(1, t - 12), min(12, t - 1) + 1):
+        monkeypatch.setenv("MOA_SPLIT_LOG2R", str(lr))
+        y, info = run(env, [n], 1, -1, x)
+        assert info["split_r"] == 1 << lr
+        err = per_transform_rel(y, ref, 1).max()
+        assert err <= TOL, (lr, err)
+
+
+@pytest.mark.parametrize("shape,batch", [((1 << 10,), 1), ((1 << 16,), 2), ((64, 32), 3), ((4096, 4096), 1),
+                                         ((16, 8, 4), 2), ((256, 256, 256), 1)])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_in_place(env, shape, batch, sign):
+    from paper_0811_2535_gb300 import inputs
+    x = inputs.uniform((batch,) + shape, 4000 + len(shape))
+    y, _ = run(env, list(shape), batch, sign, x, inplace=True)
+    err = per_transform_rel(y, oracle_ref(env, x, list(shape), batch, sign), batch)
+    assert err.max() <= TOL, err
+
+
+@pytest.mark.parametrize("shape,batch", [((2, 2), 1), ((2, 4096), 1), ((4096, 2), 1), ((8, 16), 5), ((512, 128), 2),
+                                         ((4, 8, 16), 3), ((2, 2, 2), 2), ((64, 2, 128), 1), ((32, 64, 16), 2)])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_nd_shapes(env, shape, batch, sign):
+    from paper_0811_2535_gb300 import inputs
+    x = inputs.uniform((batch,) + shape, 5000 + sum(shape))
+    y, _ = run(env, list(shape), batch, sign, x)
+    err = per_transform_rel(y, oracle_ref(env, x, list(shape), batch, sign), batch)
+    assert err.max() <= TOL, err
+
+
+def test_config_small_forward_and_round_trip(env):
+    """n = 2^10, batch 1, seed 0: forward and the inverse round trip."""
+    torch, moafft, oracle = env
+    from paper_0811_2535_gb300 import inputs
+    n = 1 << 10
+    x = inputs.uniform(n, inputs.SEED_SMALL)
+    plan = moafft.Plan([n], 1, -1)
+    X = plan.exec(torch.from_numpy(x).cuda())
+    back = plan.exec_adjoint(X).cpu().numpy() / n
+    ref = oracle.fft_radix2(x.astype(np.complex128), -1)
+    assert per_transform_rel(X.cpu().numpy(), ref, 1).max() <= TOL
+    assert per_transform_rel(back, x, 1).max() <= TOL
+
+
+@pytest.mark.parametrize("shape", [(1 << 24,), (4096, 4096), (256, 256, 256)])
+def test_config_large_full_size(env, shape):
+    """The full-size workloads (seed 1), every output element vs the oracle,
+    in the launch configuration the benchmark times."""
+    from paper_0811_2535_gb300 import inputs
+    x = inputs.uniform(shape, inputs.SEED_LARGE)
+    y, info = run(env, list(shape), 1, -1, x)
+    ref = oracle_ref(env, x, list(shape), 1, -1)
+    err = per_transform_rel(y, ref, 1).max()
+    assert err <= TOL, err
+    # elementwise: no single output far off relative to the transform's scale
+    scale = np.sqrt(np.mean(np.abs(ref) ** 2))
+    assert np.max(np.abs(y.reshape(-1) - ref.reshape(-1))) <= 50 * TOL * scale
+    if len(shape) == 1:
+        assert (info["split_r"], info["split_c"]) == (4096, 4096)
+
+
+def test_adjoint_identity_and_round_trip(env):
+    torch, moafft, _ = env
+    from paper_0811_2535_gb300 import inputs
+    for n in (1 << 9, 1 << 18):
+        x = inputs.uniform(n, 11)
+        z = inputs.uniform(n, 12)
+        plan = moafft.Plan([n], 1, -1)
+        Fx = plan.exec(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.complex128)
+        FHz = plan.exec_adjoint(torch.from_numpy(z).cuda()).cpu().numpy().astype(np.complex128)
+        lhs = np.vdot(z.astype(np.complex128), Fx)
+        rhs = np.vdot(FHz, x.astype(np.complex128))
+        assert abs(lhs - rhs) / abs(lhs) < 1e-5
+        back = plan.exec_adjoint(plan.exec(torch.from_numpy(x).cuda())).cpu().numpy() / n
+        assert per_transform_rel(back, x, 1).max() <= TOL
+
+
+def test_exec_host_end_to_end(env):
+    torch, moafft, oracle = env
+    from paper_0811_2535_gb300 import inputs
+    n = 1 << 16
+    x = inputs.uniform(n, 13)
+    plan = moafft.Plan([n], 1, -1)
+    hin = torch.from_numpy(x).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    dbuf = torch.empty(n, dtype=torch.complex64, device="cuda")
+    plan.exec_host(hin, hout, dbuf)
+    torch.cuda.current_stream().synchronize()
+    ref = oracle.fft_radix2(x.astype(np.complex128), -1)
+    assert per_transform_rel(hout.numpy(), ref, 1).max() <= TOL
+
+
+def test_exec_on_side_stream(env):
+    torch, moafft, oracle = env
+    from paper_0811_2535_gb300 import inputs
+    n = 1 << 14
+    x = inputs.uniform((4, n), 14)
+    plan = moafft.Plan([n], 4, -1)
+    s = torch.cuda.Stream()
+    xd = torch.from_numpy(x).cuda()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        y = plan.exec(xd, stream=s)
+    s.synchronize()
+    ref = oracle.fft_radix2(x.astype(np.complex128), -1)
+    assert per_transform_rel(y.cpu().numpy(), ref, 4).max() <= TOL
