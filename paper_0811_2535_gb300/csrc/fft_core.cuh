@@ -160,10 +160,32 @@ template <int LOGN> struct Sched {
 // exponent multipliers of the six stored twiddle rows
 __host__ __device__ constexpr int tw_row_k(int j) { return j < 4 ? j + 1 : (j == 4 ? 8 : 12); }
 
-// Padded shared-memory slot of element e of transform f when F transforms
-// share a tile: one element of padding per 16 keeps the stride-16 reads of
-// the radix-16 stages free of bank conflicts for every F.
-__device__ __forceinline__ int sidx(int e, int f, int logF) { return ((e + (e >> 4)) << logF) + f; }
+// Shared-memory layouts of the exchange buffer.  Element e of transform f
+// is stored at padded index pe = e + e/16 (one slot of padding per 16
+// elements, which keeps the stride-16 reads of a radix-16 stage free of
+// bank conflicts) in one of two arrangements:
+//   LAY >= 0  interleaved: slot (pe << LAY) + f, f < 2^LAY  (lanes vary f first)
+//   LAY <  0  row-major:   slot f * (N + N/16) + pe        (lanes vary e first)
+// Every index used below has the form e = w + off with a per-thread w and a
+// compile-time off, and either off is a multiple of 16 or w is; then
+// pe(w + off) = pe(w) + off + off/16 exactly, so every access is a per-thread
+// base plus an immediate offset.
+__host__ __device__ __forceinline__ constexpr int pad16(int e) { return e + (e >> 4); }
+
+template <int N, int LAY>
+struct Layout {
+    __device__ __forceinline__ static int base(int pw, int f)
+    {
+        if constexpr (LAY >= 0)
+            return (pw << LAY) + f;
+        else
+            return f * (N + N / 16) + pw;
+    }
+    __host__ __device__ static constexpr int off(int o)
+    {
+        return LAY >= 0 ? (pad16(o) << (LAY >= 0 ? LAY : 0)) : pad16(o);
+    }
+};
 
 // Multiply butterfly outputs v[1..R-1] by w_M^(u*k) from the stage table
 // (rows k = 1,2,3,4,8,12 of M1 entries each; others formed as products).
@@ -230,29 +252,33 @@ __device__ __forceinline__ void stage_compute(float2 (&v)[16], int tau, const fl
 }
 
 // Scatter stage s outputs to their Stockham positions in shared memory.
-template <int LOGN, int s>
-__device__ __forceinline__ void stage_write(const float2 (&v)[16], float2 *sm, int tau, int f, int logF)
+template <int LOGN, int s, int LAY>
+__device__ __forceinline__ void stage_write(const float2 (&v)[16], float2 *sm, int tau, int f)
 {
     using Sc = Sched<LOGN>;
+    using Ly = Layout<Sc::N, LAY>;
     constexpr int R = 1 << Sc::rlog(s);
     constexpr int NB = Sc::P / R;
     constexpr int M1 = Sc::M1(s);
-    constexpr int K = Sc::K(s);
+    constexpr int KM1 = Sc::K(s) * M1;   // = N / R, a multiple of 16
+    static_assert(KM1 % 16 == 0, "stage write offsets must be multiples of 16");
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         const int b = tau + Sc::T * i;
-        const int kappa = b / M1, u = b & (M1 - 1);
+        // e = (kappa + K*k)*M1 + u = b + (N/R)*k
+        float2 *p = sm + Ly::base(pad16(b), f);
 #pragma unroll
         for (int k = 0; k < R; ++k)
-            sm[sidx((kappa + K * k) * M1 + u, f, logF)] = v[i * R + k];
+            p[Ly::off(KM1 * k)] = v[i * R + k];
     }
 }
 
 // Gather stage s inputs from shared memory.
-template <int LOGN, int s>
-__device__ __forceinline__ void stage_read(float2 (&v)[16], const float2 *sm, int tau, int f, int logF)
+template <int LOGN, int s, int LAY>
+__device__ __forceinline__ void stage_read(float2 (&v)[16], const float2 *sm, int tau, int f)
 {
     using Sc = Sched<LOGN>;
+    using Ly = Layout<Sc::N, LAY>;
     constexpr int R = 1 << Sc::rlog(s);
     constexpr int NB = Sc::P / R;
     constexpr int M1 = Sc::M1(s);
@@ -260,36 +286,41 @@ __device__ __forceinline__ void stage_read(float2 (&v)[16], const float2 *sm, in
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         const int b = tau + Sc::T * i;
-        const int kappa = b / M1, u = b & (M1 - 1);
+        const int w = (b / M1) * M + (b & (M1 - 1));      // kappa*M + u
+        const float2 *p = sm + Ly::base(pad16(w), f);
 #pragma unroll
         for (int m = 0; m < R; ++m)
-            v[i * R + m] = sm[sidx(kappa * M + u + M1 * m, f, logF)];
+            v[i * R + m] = p[Ly::off(M1 * m)];
     }
 }
 
 // Stages 1..S-1 (stage 0 has been computed by the caller).  Every thread of
 // the block must call this (it contains block barriers).  On return the
 // thread holds outputs X[tau + T*k] in v[k], k < P.
-template <int LOGN, int s>
-__device__ __forceinline__ void run_stages(float2 (&v)[16], float2 *sm, int tau, int f, int logF,
+template <int LOGN, int s, int LAY>
+__device__ __forceinline__ void run_stages(float2 (&v)[16], float2 *sm, int tau, int f,
                                            const float2 *__restrict__ tw)
 {
     if constexpr (s < Sched<LOGN>::S) {
-        stage_write<LOGN, s - 1>(v, sm, tau, f, logF);
+        stage_write<LOGN, s - 1, LAY>(v, sm, tau, f);
         __syncthreads();
-        stage_read<LOGN, s>(v, sm, tau, f, logF);
+        stage_read<LOGN, s, LAY>(v, sm, tau, f);
         __syncthreads();
         stage_compute<LOGN, s>(v, tau, tw);
-        run_stages<LOGN, s + 1>(v, sm, tau, f, logF, tw);
+        run_stages<LOGN, s + 1, LAY>(v, sm, tau, f, tw);
     }
 }
 
-template <int LOGN>
-__device__ __forceinline__ void fft_tile(float2 (&v)[16], float2 *sm, int tau, int f, int logF,
-                                         const float2 *__restrict__ tw)
+template <int LOGN, int LAY>
+__device__ __forceinline__ void fft_tile(float2 (&v)[16], float2 *sm, int tau, int f, const float2 *__restrict__ tw)
 {
     stage_compute<LOGN, 0>(v, tau, tw);
-    run_stages<LOGN, 1>(v, sm, tau, f, logF, tw);
+    run_stages<LOGN, 1, LAY>(v, sm, tau, f, tw);
 }
+
+// Largest number of transforms per tile of the interleaved layout for
+// length 2^LOGN (tiles of 2^12 points, at least 4 transforms so column
+// accesses cover whole 32-byte sectors); the exchange buffer is sized for it.
+__host__ __device__ constexpr int max_logF_interleaved(int logN) { return logN >= 10 ? 2 : 12 - logN; }
 
 }  // namespace moa

@@ -29,6 +29,7 @@ struct PassDesc {
     int logF;       // log2 of transforms per tile
     int src, dst;   // buffer ids: 0 = user in, 1 = user out, 2 = workspace
     int tw4;        // apply the four-step twiddle (PASS_COL)
+    int pipe;       // 1: persistent TMA-pipelined kernel (pipe_kernels.cu)
 };
 
 struct TwiddleSet {
@@ -38,8 +39,16 @@ struct TwiddleSet {
 };
 
 // Launch one pass.  `flags` carries FLAG_CONJ_*; FLAG_TW4 is derived from d.
+// `status` is the plan's device status word (bounded waits report there).
 cudaError_t launch_pass(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw,
-                        int flags, cudaStream_t stream);
+                        int flags, cudaStream_t stream, int *status);
+// The pipelined strided kernels (N = 1024..4096, four transforms per tile):
+// usable when the driver exposes cuTensorMapEncodeTiled.  The input must be
+// 16-byte aligned.
+bool pipe_supported();
+cudaError_t prepare_pipe_kernels();
+cudaError_t launch_pipe_pass(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
+                             cudaStream_t stream, int *status);
 // Shared memory bytes and threads per block of a pass.
 size_t pass_smem_bytes(const PassDesc &d);
 int pass_threads(const PassDesc &d);
@@ -49,6 +58,8 @@ cudaError_t prepare_kernels();
 // Twiddle generation (FP64 on the device, rounded once to FP32).
 int stage_table_entries(int logN);
 cudaError_t generate_stage_table(float2 *dst, int logN, cudaStream_t stream);
+// dst[i] = w_modulus^(i*step mod modulus), i < count; sign -1.
+cudaError_t generate_powers(float2 *dst, int64_t count, int64_t step, int64_t modulus, cudaStream_t stream);
 // w_n^e for e < 2^h (lo) and w_n^(e*2^h) for e < n/2^h (hi); sign -1.
 cudaError_t generate_two_level(float2 *lo, float2 *hi, int logn, int h, cudaStream_t stream);
 

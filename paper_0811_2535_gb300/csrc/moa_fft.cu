@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "../../include/moa_fft.h"
+#include "fft_core.cuh"
 #include "internal.h"
 
 using moa::PassDesc;
@@ -68,10 +69,16 @@ int env_int(const char *name, int fallback)
     return (s && *s) ? std::atoi(s) : fallback;
 }
 
-// log2 of the tile size in complex elements (MOA_TILE_LOG2 overrides, 10..14)
+// log2 of the tile size in complex elements.  Small tiles let several
+// blocks share an SM, so one block's loads overlap another's arithmetic;
+// 2^12 (32 KiB) measured best for every pass whose tile can be that small.
+// A strided (column) pass needs at least 4 transforms per tile so that every
+// row segment it reads or writes is a whole 32-byte sector, and a transposed
+// row pass needs 4 rows per tile for the same reason at its store.
+// MOA_TILE_LOG2 overrides (10..14) for sweeps.
 int tile_log2()
 {
-    int t = env_int("MOA_TILE_LOG2", 14);
+    int t = env_int("MOA_TILE_LOG2", 12);
     return t < 10 ? 10 : (t > 14 ? 14 : t);
 }
 
@@ -80,6 +87,10 @@ int threads_log2_per_transform(int logN) { return logN < 4 ? 0 : logN - 4; }
 int pick_logF_col(int logN, int64_t C)
 {
     int lf = tile_log2() - logN;
+    if (lf < 2)
+        lf = 2;
+    if (lf > moa::max_logF_interleaved(logN))
+        lf = moa::max_logF_interleaved(logN);
     const int lf_threads = 10 - threads_log2_per_transform(logN);
     if (lf > lf_threads)
         lf = lf_threads;
@@ -89,9 +100,13 @@ int pick_logF_col(int logN, int64_t C)
     return lf < 0 ? 0 : lf;
 }
 
-int pick_logF_row(int logN, int64_t O)
+int pick_logF_row(int logN, int64_t O, bool transposed)
 {
     int lf = tile_log2() - logN;
+    if (transposed && lf < 2)
+        lf = 2;
+    if (transposed && lf > moa::max_logF_interleaved(logN))
+        lf = moa::max_logF_interleaved(logN);
     const int lf_threads = 10 - threads_log2_per_transform(logN);
     if (lf > lf_threads)
         lf = lf_threads;
@@ -111,7 +126,7 @@ PassDesc row_pass(int logN, int64_t O, int64_t Rt, int src, int dst)
     d.O = O;
     d.C = 1;
     d.Rt = Rt;
-    d.logF = pick_logF_row(logN, O);
+    d.logF = pick_logF_row(logN, O, Rt > 1);
     d.src = src;
     d.dst = dst;
     d.tw4 = 0;
@@ -235,6 +250,19 @@ moa_status_t allocate_and_fill(moa_fft_plan_s *p)
         return MOA_ERR_CUDA;
     if (moa::prepare_kernels() != cudaSuccess)
         return MOA_ERR_CUDA;
+    if (moa::prepare_pipe_kernels() != cudaSuccess)
+        return MOA_ERR_CUDA;
+    // the pipelined strided kernels need the tensor-map encoder; without it
+    // the plan keeps the generic kernels (same results, slower)
+    // MOA_PIPE=0 forces the generic kernels (tests compare both paths)
+    const int pipe_mode = moa::pipe_supported() ? env_int("MOA_PIPE", 1) : 0;
+    for (PassDesc &d : p->passes) {
+        const bool strided4 = d.logN >= 10 && d.logN <= 12 && d.logF == 2 &&
+                              (d.kind == moa::PASS_COL ? d.C >= 4 : d.Rt > 1);
+        d.pipe = 0;
+        if (strided4 && pipe_mode > 0)
+            d.pipe = 1;
+    }
     for (int l = 1; l <= 12; ++l) {
         p->tw.stage[l] = nullptr;
         if (offs[l]) {
@@ -280,7 +308,7 @@ moa_status_t run_pass(moa_fft_plan_s *p, size_t i, const void *in, void *out, cu
         if (i + 1 == np)
             flags |= moa::FLAG_CONJ_OUT;
     }
-    if (moa::launch_pass(d, buf(d.src), buf(d.dst), p->tw, flags, s) != cudaSuccess)
+    if (moa::launch_pass(d, buf(d.src), buf(d.dst), p->tw, flags, s, p->d_status) != cudaSuccess)
         return MOA_ERR_CUDA;
     return MOA_OK;
 }

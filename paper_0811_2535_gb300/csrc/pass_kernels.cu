@@ -9,6 +9,7 @@
 // or write F*8 contiguous bytes (F >= 4 gives whole 32-byte sectors); in the
 // row pass the F lanes that share a column index write the F outputs of the
 // four-step transpose X[k1 + r*k2] next to each other.
+
 #include "fft_core.cuh"
 #include "internal.h"
 
@@ -57,17 +58,18 @@ __global__ void __launch_bounds__(1024) col_pass_kernel(const float2 *in, float2
             v[r].y = -v[r].y;
     }
 
-    constexpr int kExchange = Sc::S > 1 ? (Sc::N + Sc::N / 16) : 0;
-    float2 *tk = smem + (kExchange << logF);
+    constexpr int LAY = max_logF_interleaved(LOGN);
+    constexpr int kExchange = Sc::S > 1 ? ((Sc::N + Sc::N / 16) << LAY) : 0;
+    float2 *tk = smem + kExchange;
     (void)tk;
     if constexpr (TW4) {
         // w_n^(col*k1), k1 = tau + T*k, as A * Tk[k]: A = w_n^(col*tau) per
         // thread, Tk[k] = w_n^(col*T*k) shared by the lanes of one column.
         for (int k = tau; k < Sc::P; k += Sc::T)
-            tk[(k << logF) + f] = two_level(tw_lo, tw_hi, tw_h, (int64_t)col * (Sc::T * k));
+            tk[(k << LAY) + f] = two_level(tw_lo, tw_hi, tw_h, (int64_t)col * (Sc::T * k));
     }
 
-    fft_tile<LOGN>(v, smem, tau, f, logF, tw);
+    fft_tile<LOGN, LAY>(v, smem, tau, f, tw);
 
     if constexpr (TW4) {
         const float2 A = two_level(tw_lo, tw_hi, tw_h, (int64_t)col * tau);
@@ -75,7 +77,7 @@ __global__ void __launch_bounds__(1024) col_pass_kernel(const float2 *in, float2
             __syncthreads();
 #pragma unroll
         for (int k = 0; k < Sc::P; ++k)
-            v[k] = cmul(v[k], cmul(A, tk[(k << logF) + f]));
+            v[k] = cmul(v[k], cmul(A, tk[(k << LAY) + f]));
     }
     if (flags & FLAG_CONJ_OUT) {
 #pragma unroll
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(1024) col_pass_kernel(const float2 *in, float2
         dst[k * step] = v[k];
 }
 
-template <int LOGN>
+template <int LOGN, bool TRANS>
 __global__ void __launch_bounds__(1024) row_pass_kernel(const float2 *in, float2 *out, int64_t O, int64_t Rt,
                                                         int logF, const float2 *__restrict__ tw, int flags)
 {
@@ -96,17 +98,23 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(const float2 *in, float2
     extern __shared__ float2 smem[];
     const int F = 1 << logF;
     const int tid = threadIdx.x;
-    const int f = tid & (F - 1);
-    const int tau = tid >> logF;
+    // Natural-order store: consecutive lanes take consecutive points of one
+    // row, so loads and stores are contiguous along the row.  Transposed
+    // store: consecutive lanes take the F rows first, so the F outputs
+    // X[k1 + r*k2], k1 = o0..o0+F-1, land side by side.
+    constexpr int LAY = TRANS ? max_logF_interleaved(LOGN) : -1;
+    const int f = TRANS ? (tid & (F - 1)) : (tid / Sc::T);
+    const int tau = TRANS ? (tid >> logF) : (tid & (Sc::T - 1));
     const int64_t o = ((int64_t)blockIdx.x << logF) + f;
     const bool active = o < O;
-
     float2 v[16];
     if (active) {
-        const float2 *src = in + o * Sc::N;
+        constexpr int R0 = 1 << Sc::rlog(0);
+        constexpr int NB0 = Sc::P / R0;
+        const float2 *src = in + o * Sc::N + tau;
 #pragma unroll
-        for (int r = 0; r < Sc::P; ++r)
-            v[r] = src[load_index<LOGN>(r, tau)];
+        for (int q = 0; q < Sc::P; ++q)
+            v[(q % NB0) * R0 + q / NB0] = src[q * Sc::T];
     } else {
 #pragma unroll
         for (int r = 0; r < Sc::P; ++r)
@@ -118,7 +126,7 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(const float2 *in, float2
             v[r].y = -v[r].y;
     }
 
-    fft_tile<LOGN>(v, smem, tau, f, logF, tw);
+    fft_tile<LOGN, LAY>(v, smem, tau, f, tw);
 
     if (flags & FLAG_CONJ_OUT) {
 #pragma unroll
@@ -127,10 +135,11 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(const float2 *in, float2
     }
     if (active) {
         const int64_t ob = o / Rt, orow = o - ob * Rt;
-        float2 *dst = out + ob * (Sc::N * Rt) + orow;
+        float2 *dst = out + ob * (Sc::N * Rt) + orow + (int64_t)tau * Rt;
+        const int64_t step = (int64_t)Sc::T * Rt;
 #pragma unroll
         for (int k = 0; k < Sc::P; ++k)
-            dst[(int64_t)(tau + Sc::T * k) * Rt] = v[k];
+            dst[k * step] = v[k];
     }
 }
 
@@ -153,8 +162,12 @@ cudaError_t launch_typed(const PassDesc &d, const float2 *in, float2 *out, const
                 in, out, (int)d.C, d.logF, logTpo, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags);
     } else {
         const int64_t grid = (d.O + (int64_t(1) << d.logF) - 1) >> d.logF;
-        row_pass_kernel<LOGN><<<(unsigned)grid, threads, smem, stream>>>(in, out, d.O, d.Rt, d.logF,
-                                                                         tw.stage[LOGN], flags);
+        if (d.Rt > 1)
+            row_pass_kernel<LOGN, true><<<(unsigned)grid, threads, smem, stream>>>(in, out, d.O, d.Rt, d.logF,
+                                                                               tw.stage[LOGN], flags);
+        else
+            row_pass_kernel<LOGN, false><<<(unsigned)grid, threads, smem, stream>>>(in, out, d.O, d.Rt, d.logF,
+                                                                                tw.stage[LOGN], flags);
     }
     return cudaGetLastError();
 }
@@ -170,7 +183,10 @@ cudaError_t set_attrs()
     e = cudaFuncSetAttribute(col_pass_kernel<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(row_pass_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    e = cudaFuncSetAttribute(row_pass_kernel<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(row_pass_kernel<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
 }
 
 }  // namespace
@@ -187,17 +203,20 @@ size_t pass_smem_bytes(const PassDesc &d)
     const int N = 1 << d.logN;
     const int P = N < 16 ? N : 16;
     const size_t F = size_t(1) << d.logF;
+    const size_t FP = size_t(1) << max_logF_interleaved(d.logN);
+    const bool interleaved = d.kind == PASS_COL || d.Rt > 1;
     size_t entries = 0;
     if (d.logN > 4)
-        entries += (size_t)(N + N / 16) * F;
+        entries += (size_t)(N + N / 16) * (interleaved ? FP : F);
     if (d.kind == PASS_COL && d.tw4)
-        entries += (size_t)P * F;
+        entries += (size_t)P * FP;
     return entries * sizeof(float2);
 }
 
 cudaError_t prepare_kernels()
 {
     cudaError_t e = cudaSuccess;
+
     if ((e = set_attrs<1>()) || (e = set_attrs<2>()) || (e = set_attrs<3>()) || (e = set_attrs<4>()) ||
         (e = set_attrs<5>()) || (e = set_attrs<6>()) || (e = set_attrs<7>()) || (e = set_attrs<8>()) ||
         (e = set_attrs<9>()) || (e = set_attrs<10>()) || (e = set_attrs<11>()) || (e = set_attrs<12>()))
@@ -206,8 +225,10 @@ cudaError_t prepare_kernels()
 }
 
 cudaError_t launch_pass(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
-                        cudaStream_t stream)
+                        cudaStream_t stream, int *status)
 {
+    if (d.pipe && (reinterpret_cast<uintptr_t>(in) & 15) == 0)
+        return launch_pipe_pass(d, in, out, tw, flags, stream, status);
     switch (d.logN) {
     case 1: return launch_typed<1>(d, in, out, tw, flags, stream);
     case 2: return launch_typed<2>(d, in, out, tw, flags, stream);

@@ -1,0 +1,466 @@
+// Pipelined strided passes for N = 1024..4096 with four transforms per tile.
+//
+// These are the two halves of the dimension-lifted transform that touch
+// memory with a stride: the column pass (paper's block phase, Fig. 4.8-4.9:
+// r-point transforms down the columns of the r x c array, then the twiddle
+// w_n^(j2*k1)) and the transposed row pass (cyclic phase: c-point
+// transforms along rows, stored at X[k1 + r*k2]).  Four transforms per tile
+// make every row segment a whole 32-byte sector; with N = 4096 that tile is
+// 128 KiB, so only one tile fits an SM (registers hold the tile being
+// computed, shared memory its exchange buffer).  To keep HBM busy anyway
+// each block is persistent and refills its shared memory asynchronously:
+//
+//   H (first-half landing buffer, N/2 x 4 complex64): TMA brings the first
+//     half of tile i+1 (cp.async.bulk.tensor 2-D boxes of 256 rows x 32 bytes
+//     for columns, 1-D cp.async.bulk copies for rows) while tile i computes;
+//   E (exchange buffer, (N + N/16) x 4 complex64): the single-round register
+//     exchanges of tile i's radix-16 stages; as soon as the last exchange has
+//     been read, TMA lands the second half of tile i+1 in it, overlapping the
+//     last stage, the epilogue and the stores of tile i.
+//
+// Completion is tracked on two mbarriers.  One elected thread waits on them
+// with an iteration limit; on timeout it records MOA_ERR_TIMEOUT in the
+// status word and the whole block returns.
+#include <cuda.h>
+
+#include "fft_core.cuh"
+#include "internal.h"
+
+namespace moa {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Upper bound on mbarrier polls before a wait is declared failed (each
+// try_wait may suspend the thread for a while; a normal tile load completes
+// within a few thousand polls).
+constexpr uint32_t kMaxPolls = 1u << 26;
+
+__device__ __forceinline__ float2 two_level_tw(const float2 *__restrict__ lo, const float2 *__restrict__ hi, int h,
+                                               int64_t e)
+{
+    return cmul(__ldg(&lo[e & ((int64_t(1) << h) - 1)]), __ldg(&hi[e >> h]));
+}
+
+struct PipeSmem {
+    // entries (float2) of the exchange buffer E, which also lands the second
+    // half of the next tile, and of the first-half landing buffer H
+    template <int LOGN> __host__ __device__ static constexpr int E_entries() { return ((1 << LOGN) + (1 << LOGN) / 16) * 4; }
+    template <int LOGN> __host__ __device__ static constexpr int row_pitch() { return (1 << LOGN) / 2 + 4; }
+    template <int LOGN> __host__ __device__ static constexpr int H_entries() { return 4 * row_pitch<LOGN>(); }
+    template <int LOGN> __host__ __device__ static constexpr size_t bytes()
+    {
+        return (size_t)(E_entries<LOGN>() + H_entries<LOGN>() + 64) * 8 + 64;
+    }
+};
+
+// Bounded wait on an mbarrier phase by one thread; on timeout the status word
+// gets MOA_ERR_TIMEOUT and *abort_flag is set.
+__device__ __forceinline__ void bounded_wait(uint64_t *bar, uint32_t parity, int *status, int *abort_flag)
+{
+    uint32_t polls = 0;
+    while (!mbar_try_wait(bar, parity)) {
+        if (++polls >= kMaxPolls) {
+            atomicExch(status, 6);   // MOA_ERR_TIMEOUT
+            *abort_flag = 1;
+            return;
+        }
+    }
+}
+
+// The three radix stages of N = 1024, 2048, 4096 (radix 4/8/16, 16, 16) with
+// single-round exchanges through E; `after_last_read` runs once E is no
+// longer needed (used to start refilling it).
+template <int LOGN, typename F>
+__device__ __forceinline__ void three_stages(float2 (&v)[16], float2 *E, int tau, int f, const float2 *__restrict__ tw,
+                                             F after_last_read)
+{
+    static_assert(Sched<LOGN>::S == 3, "three-stage schedule expected");
+    stage_compute<LOGN, 0>(v, tau, tw);
+    stage_write<LOGN, 0, 2>(v, E, tau, f);
+    __syncthreads();
+    stage_read<LOGN, 1, 2>(v, E, tau, f);
+    __syncthreads();
+    stage_compute<LOGN, 1>(v, tau, tw);
+    stage_write<LOGN, 1, 2>(v, E, tau, f);
+    __syncthreads();
+    stage_read<LOGN, 2, 2>(v, E, tau, f);
+    __syncthreads();
+    after_last_read();
+    stage_compute<LOGN, 2>(v, tau, tw);
+}
+
+// Column pass: view [O][N][C], tile = 4 consecutive columns of one o.
+template <int LOGN, bool TW4>
+__global__ void __launch_bounds__(1 << (LOGN - 2), 1)
+    pipe_col_kernel(const __grid_constant__ CUtensorMap tmap, float2 *out, int C, int logTpo, int ntiles,
+                    const float2 *__restrict__ tw, const float2 *__restrict__ tw_lo, const float2 *__restrict__ tw_hi,
+                    int tw_h, int flags, int *status)
+{
+    using Sc = Sched<LOGN>;
+    constexpr int N = Sc::N, T = Sc::T, NH = N / 2;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    float2 *E = reinterpret_cast<float2 *>(smem_raw);
+    float2 *H = E + PipeSmem::E_entries<LOGN>();
+    float2 *tk = H + PipeSmem::H_entries<LOGN>();    // [16][4] four-step twiddle factors
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tk + 64);   // [0]: H, [1]: second half in E
+    int *abort_flag = reinterpret_cast<int *>(bar + 2);
+
+    const int tid = threadIdx.x;
+    const int f = tid & 3, tau = tid >> 2;
+    const unsigned tpo_mask = (1u << logTpo) - 1;
+
+    // rows [h*N/2, (h+1)*N/2) of the tile's four columns, as boxes of 256 rows x 32 bytes
+    auto issue_half = [&](int tile, int h, float2 *dst, uint64_t *b) {
+        const int o = tile >> logTpo;
+        const int c0 = (tile & tpo_mask) << 2;
+        mbar_arrive_expect_tx(b, NH * 4 * (uint32_t)sizeof(float2));
+#pragma unroll
+        for (int k = 0; k < NH / 256; ++k)
+            tma_load_2d(dst + k * 256 * 4, &tmap, b, 2 * c0, o * N + h * NH + k * 256);
+    };
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        *abort_flag = 0;
+    }
+    __syncthreads();
+    int tile = blockIdx.x;
+    if (tid == 0 && tile < ntiles) {
+        issue_half(tile, 0, H, &bar[0]);
+        issue_half(tile, 1, E, &bar[1]);
+    }
+    uint32_t parity = 0;
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int o = tile >> logTpo;
+        const int col = ((tile & tpo_mask) << 2) + f;
+        const int next = tile + (int)gridDim.x;
+        if (tid == 0) {
+            bounded_wait(&bar[0], parity, status, abort_flag);
+            bounded_wait(&bar[1], parity, status, abort_flag);
+        }
+        __syncthreads();
+        if (*abort_flag)
+            return;
+        parity ^= 1u;
+
+        // element tau + T*q lands in register (q % NB0)*R0 + q / NB0 (stage-0 order);
+        // q < 8 is in the first half (H), q >= 8 in the second (E)
+        constexpr int R0 = 1 << Sc::rlog(0), NB0 = 16 / R0;
+        float2 v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const float2 *src = q < 8 ? H : E;
+            v[(q % NB0) * R0 + q / NB0] = src[(tau + T * (q & 7)) * 4 + f];
+        }
+        __syncthreads();   // H and E have been read
+        if (tid == 0 && next < ntiles) {
+            fence_proxy_async();
+            issue_half(next, 0, H, &bar[0]);
+        }
+        if (flags & FLAG_CONJ_IN) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+                v[r].y = -v[r].y;
+        }
+        if constexpr (TW4) {
+            if (tau < 16)
+                tk[tau * 4 + f] = two_level_tw(tw_lo, tw_hi, tw_h, (int64_t)col * (T * tau));
+        }
+
+        three_stages<LOGN>(v, E, tau, f, tw, [&] {
+            if (tid == 0 && next < ntiles) {
+                fence_proxy_async();
+                issue_half(next, 1, E, &bar[1]);
+            }
+        });
+
+        if constexpr (TW4) {
+            const float2 A = two_level_tw(tw_lo, tw_hi, tw_h, (int64_t)col * tau);
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                v[k] = cmul(v[k], cmul(A, tk[k * 4 + f]));
+        }
+        if (flags & FLAG_CONJ_OUT) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                v[k].y = -v[k].y;
+        }
+        float2 *dst = out + (int64_t)o * N * C + col + (int64_t)tau * C;
+        const int64_t step = (int64_t)T * C;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            dst[k * step] = v[k];
+    }
+}
+
+// Transposed row pass: rows o = 4*tile + f of the [O][N] view; output
+// element k of row o goes to (o / Rt)*(N*Rt) + (o % Rt) + Rt*k.
+template <int LOGN>
+__global__ void __launch_bounds__(1 << (LOGN - 2), 1)
+    pipe_rowT_kernel(const float2 *in, float2 *out, int64_t O, int64_t Rt, int ntiles,
+                     const float2 *__restrict__ tw, int flags, int *status)
+{
+    using Sc = Sched<LOGN>;
+    constexpr int N = Sc::N, T = Sc::T, NH = N / 2;
+    constexpr int PITCH = PipeSmem::row_pitch<LOGN>();
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    float2 *E = reinterpret_cast<float2 *>(smem_raw);
+    float2 *H = E + PipeSmem::E_entries<LOGN>();
+    uint64_t *bar = reinterpret_cast<uint64_t *>(H + PipeSmem::H_entries<LOGN>() + 64);
+    int *abort_flag = reinterpret_cast<int *>(bar + 2);
+
+    const int tid = threadIdx.x;
+    const int f = tid & 3, tau = tid >> 2;
+
+    auto issue_half = [&](int tile, int h, float2 *dst, uint64_t *b) {
+        const int64_t o0 = (int64_t)tile * 4;
+        const int rows = (int)((O - o0) < 4 ? (O - o0) : 4);
+        mbar_arrive_expect_tx(b, rows * NH * (uint32_t)sizeof(float2));
+        for (int r = 0; r < rows; ++r)
+            bulk_load(dst + r * PITCH, in + (o0 + r) * N + h * NH, NH * (uint32_t)sizeof(float2), b);
+    };
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        *abort_flag = 0;
+    }
+    __syncthreads();
+    int tile = blockIdx.x;
+    if (tid == 0 && tile < ntiles) {
+        issue_half(tile, 0, H, &bar[0]);
+        issue_half(tile, 1, E, &bar[1]);
+    }
+    uint32_t parity = 0;
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int64_t o = (int64_t)tile * 4 + f;
+        const bool active = o < O;
+        const int next = tile + (int)gridDim.x;
+        if (tid == 0) {
+            bounded_wait(&bar[0], parity, status, abort_flag);
+            bounded_wait(&bar[1], parity, status, abort_flag);
+        }
+        __syncthreads();
+        if (*abort_flag)
+            return;
+        parity ^= 1u;
+
+        constexpr int R0 = 1 << Sc::rlog(0), NB0 = 16 / R0;
+        float2 v[16];
+        if (active) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float2 *src = q < 8 ? H : E;
+                v[(q % NB0) * R0 + q / NB0] = src[f * PITCH + tau + T * (q & 7)];
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                v[q] = make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        if (tid == 0 && next < ntiles) {
+            fence_proxy_async();
+            issue_half(next, 0, H, &bar[0]);
+        }
+        if (flags & FLAG_CONJ_IN) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+                v[r].y = -v[r].y;
+        }
+
+        three_stages<LOGN>(v, E, tau, f, tw, [&] {
+            if (tid == 0 && next < ntiles) {
+                fence_proxy_async();
+                issue_half(next, 1, E, &bar[1]);
+            }
+        });
+
+        if (flags & FLAG_CONJ_OUT) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                v[k].y = -v[k].y;
+        }
+        if (active) {
+            const int64_t ob = o / Rt, orow = o - ob * Rt;
+            float2 *dst = out + ob * (N * Rt) + orow + (int64_t)tau * Rt;
+            const int64_t step = (int64_t)T * Rt;
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                dst[k * step] = v[k];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side: tensor-map encoding through the driver entry point (no libcuda
+// link), launch configuration, dispatch.
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+template <int LOGN> size_t col_smem() { return PipeSmem::bytes<LOGN>(); }
+template <int LOGN> size_t rowT_smem() { return PipeSmem::bytes<LOGN>(); }
+
+int g_num_sms = 0;
+
+template <int LOGN>
+cudaError_t launch_col(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
+                       cudaStream_t stream, int *status)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc)
+        return cudaErrorNotSupported;
+    CUtensorMap map;
+    const cuuint64_t dims[2] = {(cuuint64_t)(2 * d.C), (cuuint64_t)(d.O << LOGN)};
+    const cuuint64_t strides[1] = {(cuuint64_t)(2 * d.C * sizeof(float))};
+    const cuuint32_t box[2] = {8, 256};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2 *>(in), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    int logTpo = 0;
+    while ((int64_t(1) << logTpo) < (d.C >> 2))
+        ++logTpo;
+    const int ntiles = (int)(d.O << logTpo);
+    const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
+    const size_t smem = col_smem<LOGN>();
+    if (d.tw4)
+        pipe_col_kernel<LOGN, true><<<grid, 1 << (LOGN - 2), smem, stream>>>(
+            map, out, (int)d.C, logTpo, ntiles, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags, status);
+    else
+        pipe_col_kernel<LOGN, false><<<grid, 1 << (LOGN - 2), smem, stream>>>(
+            map, out, (int)d.C, logTpo, ntiles, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags, status);
+    return cudaGetLastError();
+}
+
+template <int LOGN>
+cudaError_t launch_rowT(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
+                        cudaStream_t stream, int *status)
+{
+    const int ntiles = (int)((d.O + 3) / 4);
+    const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
+    pipe_rowT_kernel<LOGN><<<grid, 1 << (LOGN - 2), rowT_smem<LOGN>(), stream>>>(in, out, d.O, d.Rt, ntiles,
+                                                                                  tw.stage[LOGN], flags, status);
+    return cudaGetLastError();
+}
+
+template <int LOGN>
+cudaError_t set_pipe_attrs()
+{
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(pipe_col_kernel<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)col_smem<LOGN>())) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(pipe_col_kernel<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)col_smem<LOGN>())) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(pipe_rowT_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)rowT_smem<LOGN>());
+}
+
+}  // namespace
+
+bool pipe_supported() { return encode_fn() != nullptr; }
+
+cudaError_t prepare_pipe_kernels()
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if ((e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    if ((e = set_pipe_attrs<10>()) || (e = set_pipe_attrs<11>()) || (e = set_pipe_attrs<12>()))
+        return e;
+    return cudaSuccess;
+}
+
+cudaError_t launch_pipe_pass(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
+                             cudaStream_t stream, int *status)
+{
+    if (d.kind == PASS_COL) {
+        switch (d.logN) {
+        case 10: return launch_col<10>(d, in, out, tw, flags, stream, status);
+        case 11: return launch_col<11>(d, in, out, tw, flags, stream, status);
+        case 12: return launch_col<12>(d, in, out, tw, flags, stream, status);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (d.logN) {
+    case 10: return launch_rowT<10>(d, in, out, tw, flags, stream, status);
+    case 11: return launch_rowT<11>(d, in, out, tw, flags, stream, status);
+    case 12: return launch_rowT<12>(d, in, out, tw, flags, stream, status);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace moa

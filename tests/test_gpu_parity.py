@@ -188,3 +188,21 @@ def test_exec_on_side_stream(env):
     s.synchronize()
     ref = oracle.fft_radix2(x.astype(np.complex128), -1)
     assert per_transform_rel(y.cpu().numpy(), ref, 4).max() <= TOL
+
+
+@pytest.mark.parametrize("shape,batch", [((1 << 20,), 1), ((1 << 22,), 1), ((1 << 24,), 1), ((1 << 21,), 3),
+                                         ((4096, 4096), 1), ((2048, 1024), 2), ((1024, 8), 3)])
+def test_pipelined_and_generic_kernels_agree(env, shape, batch, monkeypatch):
+    """The persistent TMA-pipelined strided kernels and the generic kernels
+    compute the same transform (both checked against the oracle)."""
+    from paper_0811_2535_gb300 import inputs
+    x = inputs.uniform((batch,) + shape, 6000 + len(shape))
+    ref = oracle_ref(env, x, list(shape), batch, -1)
+    ys = []
+    for pipe in ("1", "0"):
+        monkeypatch.setenv("MOA_PIPE", pipe)
+        for sign in (-1,):
+            y, _ = run(env, list(shape), batch, sign, x)
+            assert per_transform_rel(y, ref, batch).max() <= TOL, pipe
+            ys.append(y)
+    assert per_transform_rel(ys[0], ys[1], batch).max() <= TOL
