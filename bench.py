@@ -57,16 +57,6 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def csrc_hash() -> str:
-    h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_0811_2535_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
-        with open(os.path.join(d, name), "rb") as fh:
-            h.update(name.encode())
-            h.update(fh.read())
-    return h.hexdigest()[:16]
-
-
 def load_traffic(kernel_key: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources (else None)."""
@@ -74,7 +64,7 @@ def load_traffic(kernel_key: str):
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             t = json.load(fh)
         ent = t.get("kernels", {}).get(kernel_key)
-        if ent and t.get("csrc_hash") == csrc_hash():
+        if ent and ent.get("src_hash") == kernel_src_hash(kernel_key):
             return float(ent["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -142,6 +132,36 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(value: float, world: int) -> float:
+    """Max of a per-rank scalar over all ranks (identity when world == 1)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gflops(flops_per_step: float, steps: int, world: int, max_ms: float) -> float:
+    """Aggregate throughput: every rank runs its own step (replicas), the job
+    time is the slowest rank's."""
+    return world * flops_per_step * steps / (max_ms * 1e-3) / 1e9
+
+
+def kernel_src_hash(kernel: str) -> str:
+    """Hash of the source files a kernel is built from (its family)."""
+    d = os.path.join(ROOT, "paper_0811_2535_gb300", "csrc")
+    own = "pipe_kernels.cu" if kernel.startswith("pipe_") else "pass_kernels.cu"
+    h = hashlib.sha256()
+    for name in (own, "fft_core.cuh", "internal.h"):
+        with open(os.path.join(d, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def oracle_step(shapes, seed):
     """Run the FP64 oracle on the given shapes; returns (seconds, outputs)."""
     import numpy as np
@@ -197,14 +217,6 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
     return 0
 
-# kernel launched by each pass of each workload (template name as ncu lists it)
-PASS_KERNELS = {
-    "1d_2^24": ["col_pass_kernel<12,true>", "row_pass_kernel<12>"],
-    "2d_4096^2": ["row_pass_kernel<12>", "col_pass_kernel<12,false>"],
-    "3d_256^3": ["row_pass_kernel<8>", "col_pass_kernel<8,false>", "col_pass_kernel<8,false>"],
-}
-
-
 def run_moa(args):
     import numpy as np
     import torch
@@ -221,16 +233,15 @@ def run_moa(args):
     _build.build()
     moafft.lib()
 
-    plans, xs, outs = [], [], []
+    plans, xs, outs, pass_kernels = [], [], [], {}
     for name, shape in WORKLOAD:
         p = moafft.Plan(list(shape), 1, -1)
-        info = p.info()
-        assert info["passes"] == len(PASS_KERNELS[name]), (name, info)
+        pass_kernels[name] = [p.pass_info(i)["kernel"] for i in range(p.info()["passes"])]
         plans.append(p)
         xs.append(torch.from_numpy(inputs.uniform(shape, inputs.SEED_LARGE)).to(dev))
         outs.append(torch.empty(numel(shape), dtype=torch.complex64, device=dev))
     stream = torch.cuda.current_stream(dev)
-    npass = [len(PASS_KERNELS[name]) for name, _ in WORKLOAD]
+    npass = [len(pass_kernels[name]) for name, _ in WORKLOAD]
     launches_per_step = sum(npass)
 
     def step(events=None, ei=0):
@@ -283,16 +294,13 @@ def run_moa(args):
     k = 0
     for _ in range(args.steps):
         for name, _shape in WORKLOAD:
-            for kname in PASS_KERNELS[name]:
+            for kname in pass_kernels[name]:
                 per_kernel.setdefault((name, kname), []).append(events[k].elapsed_time(events[k + 1]))
                 k += 1
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world)
     ms_per_step = total_ms / args.steps
     f_step = sum(flops(s) for _, s in WORKLOAD)
-    value = world * f_step * args.steps / (total_ms * 1e-3) / 1e9
+    value = whole_job_gflops(f_step, args.steps, world, total_ms)
 
     # roofline of the dominant kernel (largest share of the step time)
     by_kernel = {}
@@ -309,6 +317,11 @@ def run_moa(args):
     kernels = {f"{name}:{kname}": {"avg_us": statistics.mean(ds) * 1e3,
                                    "GB_per_s": bytes_per_launch / (statistics.mean(ds) * 1e-3) / 1e9}
                for (name, kname), ds in per_kernel.items()}
+    # the lifted 1-D transform as a whole: two passes, 32n algorithmic bytes
+    t1d = sum(statistics.mean(ds) for (name, _k), ds in per_kernel.items() if name == "1d_2^24")
+    lifted = {"time_us": t1d * 1e3, "algorithmic_bytes": 2 * bytes_per_launch,
+              "achieved_GBps": 2 * bytes_per_launch / (t1d * 1e-3) / 1e9}
+    lifted["frac"] = lifted["achieved_GBps"] / peak
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     e2e_steps = max(1, min(args.steps, 10))
@@ -328,13 +341,9 @@ def run_moa(args):
             p.exec_host(a, b, d, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
     io_bytes = sum(8 * numel(s) for _, s in WORKLOAD)
-    e2e = {"value": world * f_step * e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+    e2e = {"value": whole_job_gflops(f_step, e2e_steps, world, e2e_ms), "unit": "GFLOP/s",
            "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes}
 
     for p in plans:
@@ -348,7 +357,7 @@ def run_moa(args):
                 "config": {"workload": WORKLOAD_NAME, "l2": "inputs larger than L2 (128 MiB each), no flush",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "passes_per_step": launches_per_step},
-                "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
+                "roofline": roofline, "lifted_1d": lifted, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches_per_step * args.steps, "rel_l2": parity or None,
                 "parity_ok": (all(v <= TOL for v in parity.values()) if parity else None), "kernels": kernels}
         print(json.dumps(line), flush=True)

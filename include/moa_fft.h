@@ -131,6 +131,14 @@ MOA_API const char *moa_fft_error_string(moa_status_t status);
 MOA_API moa_status_t moa_fft_plan_info(moa_fft_plan_t plan, int *passes, int64_t *split_r,
                                int64_t *split_c, size_t *workspace_bytes);
 
+/* Describe pass `index` of the plan (0 <= index < passes): the name of the
+ * kernel it launches, written NUL-terminated into name[0..name_len-1]
+ * (truncated if needed; name may be NULL when name_len is 0), and its
+ * algorithmic HBM bytes per exec (complex64 elements read plus written, 8
+ * bytes each).  Instrumentation for per-kernel roofline reports. */
+MOA_API moa_status_t moa_fft_pass_info(moa_fft_plan_t plan, int index, char *name, size_t name_len,
+                                       int64_t *bytes);
+
 /* Destroy a plan and free everything it owns.  NULL is a no-op (MOA_OK);
  * a handle that is not a live plan returns MOA_ERR_INVALID_ARG. */
 MOA_API moa_status_t moa_fft_destroy(moa_fft_plan_t plan);

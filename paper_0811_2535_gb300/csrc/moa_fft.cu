@@ -14,13 +14,14 @@
 //     the others.
 #include <cuda_runtime.h>
 
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <set>
 #include <vector>
 
-#include "../../include/moa_fft.h"
+#include "moa_fft.h"
 #include "fft_core.cuh"
 #include "internal.h"
 
@@ -480,6 +481,30 @@ moa_status_t moa_fft_plan_info(moa_fft_plan_t plan, int *passes, int64_t *split_
         *split_c = plan->split_c;
     if (workspace_bytes)
         *workspace_bytes = plan->workspace_bytes;
+    return MOA_OK;
+}
+
+moa_status_t moa_fft_pass_info(moa_fft_plan_t plan, int index, char *name, size_t name_len, int64_t *bytes)
+{
+    if (!is_live(plan) || index < 0 || (size_t)index >= plan->passes.size())
+        return MOA_ERR_INVALID_ARG;
+    if (name_len > 0 && !name)
+        return MOA_ERR_INVALID_ARG;
+    const PassDesc &d = plan->passes[index];
+    char buf[64];
+    if (d.pipe)
+        snprintf(buf, sizeof(buf), d.kind == moa::PASS_COL ? "pipe_col_kernel<%d,%d>" : "pipe_rowT_kernel<%d>",
+                 d.logN, d.tw4);
+    else if (d.kind == moa::PASS_COL)
+        snprintf(buf, sizeof(buf), "col_pass_kernel<%d,%d>", d.logN, d.tw4);
+    else
+        snprintf(buf, sizeof(buf), "row_pass_kernel<%d,%d>", d.logN, d.Rt > 1 ? 1 : 0);
+    if (name_len > 0) {
+        strncpy(name, buf, name_len - 1);
+        name[name_len - 1] = '\0';
+    }
+    if (bytes)
+        *bytes = 2 * (int64_t)sizeof(float2) * plan->total;
     return MOA_OK;
 }
 

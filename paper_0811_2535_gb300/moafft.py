@@ -38,6 +38,7 @@ SIGNATURES = {
     "moa_fft_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "moa_fft_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64),
                                          ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_size_t)]),
+    "moa_fft_pass_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(_I64)]),
     "moa_fft_destroy": (ctypes.c_int, [_P]),
 }
 
@@ -151,6 +152,13 @@ class Plan:
         _check(lib().moa_fft_plan_info(self._h, ctypes.byref(p), ctypes.byref(r), ctypes.byref(c), ctypes.byref(w)),
                "moa_fft_plan_info")
         return {"passes": p.value, "split_r": r.value, "split_c": c.value, "workspace_bytes": w.value}
+
+    def pass_info(self, index: int) -> dict:
+        """Kernel name and algorithmic bytes of pass ``index``."""
+        buf = ctypes.create_string_buffer(64)
+        b = _I64()
+        _check(lib().moa_fft_pass_info(self._h, int(index), buf, 64, ctypes.byref(b)), "moa_fft_pass_info")
+        return {"kernel": buf.value.decode(), "bytes": b.value}
 
     def destroy(self) -> None:
         if getattr(self, "_h", None):

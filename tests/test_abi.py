@@ -96,6 +96,7 @@ def test_dead_handles_and_null(L):
     assert L.moa_fft_plan_info(bogus, None, None, None, None) == 1
     assert L.moa_fft_exec_host(bogus, None, None, None, None) == 1
     assert L.moa_fft_exec_pass(bogus, 0, -1, None, None, None) == 1
+    assert L.moa_fft_pass_info(bogus, 0, None, 0, None) == 1
 
 
 def test_error_strings(L):
