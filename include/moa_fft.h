@@ -117,6 +117,25 @@ MOA_API moa_status_t moa_fft_exec_pass(moa_fft_plan_t plan, int index, int sign,
 MOA_API moa_status_t moa_fft_exec_host(moa_fft_plan_t plan, const void *host_in, void *host_out,
                                void *dev_buf, void *stream);
 
+/* Allocation-free 1-D transform, for callers that cannot allocate device
+ * memory (a custom allocator owns all of it, or the calling path must never
+ * enter the CUDA allocator).  The paper has no counterpart: this is a
+ * deployment variant of moa_fft_exec with no plan.
+ *   in, out : caller-owned device pointers to n complex64 values, 8-byte
+ *             aligned; in == out allowed.
+ *   n       : power of two, 2 <= n <= 2^20 (1,048,576).  Larger n returns
+ *             MOA_ERR_UNSUPPORTED: the transform's scratch lives in a fixed
+ *             8 MiB static device array.
+ *   sign    : -1 or +1, as for moa_fft_plan.  stream: cudaStream_t or NULL.
+ * Same kernels and results as a plan with batch 1.  Nothing is allocated:
+ * the scratch and the twiddle tables (about 8.3 MiB in all) are static
+ * device arrays that every GPU using this library holds until the process
+ * exits.  The first call on a device sets them up (symbol lookup, twiddle
+ * generation) and synchronises `stream` once: make that first call before
+ * any stream capture.  All calls on a device share the arrays; calls that
+ * overlap on the GPU race and must be serialised by the caller. */
+MOA_API moa_status_t moa_fft_exec_noalloc(const void *in, void *out, int64_t n, int sign, void *stream);
+
 /* Device status word of the plan (MOA_OK or the first error a kernel
  * recorded), read with a synchronous copy; the word is then reset to
  * MOA_OK. */
