@@ -217,6 +217,60 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
     return 0
 
+def graph_time_ms(torch, fn, iters):
+    """Mean time of `fn(stream)` replayed from a captured CUDA graph."""
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fn(s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn(torch.cuda.current_stream())
+    for _ in range(2):
+        g.replay()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(iters):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / iters
+
+
+def batched_report(torch, moafft, inputs, dev, iters):
+    """Uneven batch (4096 transforms of 2^k points, k ~ U{6..16}, seed 2):
+    the one persistent launch vs a launch loop of per-size plans, both
+    replayed from CUDA graphs."""
+    import numpy as np
+    lengths, vecs = inputs.uneven_batch(4096, inputs.SEED_UNEVEN)
+    lengths = [int(n) for n in lengths]
+    x = torch.from_numpy(np.concatenate(vecs)).to(dev)
+    out = torch.empty_like(x)
+    f = sum(flops((n,)) for n in lengths)
+    alg = 16.0 * sum(lengths)
+    bp = moafft.BatchedPlan(lengths, -1)
+    t_batch = graph_time_ms(torch, lambda st: bp.exec(x, out, stream=st), iters)
+    plans = {n: moafft.Plan([n], 1, -1) for n in sorted(set(lengths))}
+    offs = bp.offsets()
+
+    def loop(st):
+        for o, n in zip(offs, lengths):
+            plans[n].exec(x[o:o + n], out[o:o + n], stream=st)
+    t_loop = graph_time_ms(torch, loop, 2)
+    bp.destroy()
+    for p in plans.values():
+        p.destroy()
+    return {"workload": "4096 x 1-D 2^k, k ~ U{6..16} (seed 2), N(0,1), complex64 forward",
+            "persistent_graph_us": t_batch * 1e3, "persistent_GFLOPs": f / t_batch / 1e6,
+            "persistent_algorithmic_GBps": alg / t_batch / 1e6,
+            "launch_loop_graph_us": t_loop * 1e3, "launch_loop_GFLOPs": f / t_loop / 1e6,
+            "speedup": t_loop / t_batch}
+
+
 def run_moa(args):
     import numpy as np
     import torch
@@ -349,6 +403,7 @@ def run_moa(args):
     for p in plans:
         if p.status() != 0:
             raise RuntimeError("device status word set after the benchmark")
+    batched = None if args.no_batched else batched_report(torch, moafft, inputs, dev, max(3, min(args.steps, 20)))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -357,7 +412,7 @@ def run_moa(args):
                 "config": {"workload": WORKLOAD_NAME, "l2": "inputs larger than L2 (128 MiB each), no flush",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "passes_per_step": launches_per_step},
-                "roofline": roofline, "lifted_1d": lifted, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
+                "roofline": roofline, "lifted_1d": lifted, "batched_uneven": batched, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches_per_step * args.steps, "rel_l2": parity or None,
                 "parity_ok": (all(v <= TOL for v in parity.values()) if parity else None), "kernels": kernels}
         print(json.dumps(line), flush=True)
@@ -373,6 +428,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["moa", "reference"], default="moa")
     ap.add_argument("--no-oracle", action="store_true", help="skip the CPU oracle parity/baseline leg")
+    ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -17,12 +17,14 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <set>
 #include <vector>
 
 #include "moa_fft.h"
 #include "fft_core.cuh"
+#include "batched.h"
 #include "internal.h"
 
 using moa::PassDesc;
@@ -41,6 +43,10 @@ struct moa_fft_plan_s {
     float2 *workspace = nullptr;
     size_t workspace_bytes = 0;
     int *d_status = nullptr;
+    // batched plans (moa_fft_plan_batched): one persistent launch
+    bool batched = false;
+    moa::BatchLaunch bl{};
+    void *batch_block = nullptr;  // tasks, offsets, ticket, table pointers
 };
 
 namespace {
@@ -164,6 +170,9 @@ cudaError_t dev_alloc(void **p, size_t bytes)
 
 void free_plan_memory(moa_fft_plan_s *p)
 {
+    if (p->batch_block)
+        cudaFree(p->batch_block);
+    p->batch_block = nullptr;
     if (p->dev_block)
         cudaFree(p->dev_block);
     if (p->workspace)
@@ -293,8 +302,204 @@ moa_status_t check_io(const void *in, const void *out)
     return MOA_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Batched plans: transforms of uneven lengths in one persistent launch.
+
+// Split of a large transform (2^13..2^16 points) handled inside one block:
+// both factors in [16, 1024] (so every tile holds at least four transforms);
+// default r = 2^floor(log n / 2), MOA_BATCH_LOG2R overrides within range.
+int batched_logr(int logn)
+{
+    const int lo = std::max(4, logn - 10), hi = std::min(10, logn - 4);
+    int lr = env_int("MOA_BATCH_LOG2R", logn / 2);
+    if (lr < lo || lr > hi)
+        lr = std::min(std::max(logn / 2, lo), hi);
+    return lr;
+}
+
+moa_status_t build_batched(moa_fft_plan_s *p, const int64_t *lengths, int64_t count)
+{
+    std::vector<int64_t> offset(count);
+    int64_t total = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        offset[i] = total;
+        total += lengths[i];
+    }
+    p->total = total;
+    p->batch = 1;
+    p->dims = 1;
+    p->batched = true;
+
+    // group by length, longest first
+    std::vector<int64_t> offs_sorted;
+    offs_sorted.reserve(count);
+    std::vector<moa::BatchTask> small;
+    std::vector<double> small_cost;
+    std::vector<int> large;   // positions in offs_sorted of the large transforms, longest first
+    std::vector<int8_t> large_logn;
+    bool need_stage[13] = {false};
+    bool need_lift[17] = {false};
+    for (int logn = 16; logn >= 1; --logn) {
+        std::vector<int64_t> group;
+        for (int64_t i = 0; i < count; ++i)
+            if (ilog2(lengths[i]) == logn)
+                group.push_back(offset[i]);
+        if (group.empty())
+            continue;
+        const int first = (int)offs_sorted.size();
+        offs_sorted.insert(offs_sorted.end(), group.begin(), group.end());
+        if (logn >= 13) {
+            const int lr = batched_logr(logn);
+            need_stage[lr] = need_stage[logn - lr] = true;
+            need_lift[logn] = true;
+            for (size_t k = 0; k < group.size(); ++k) {
+                large.push_back(first + (int)k);
+                large_logn.push_back((int8_t)logn);
+            }
+        } else {
+            need_stage[logn] = true;
+            const int fmax = logn <= 4 ? 256 : (4096 >> logn);
+            for (size_t k = 0; k < group.size(); k += fmax) {
+                const int cnt = (int)std::min<size_t>(fmax, group.size() - k);
+                small.push_back(moa::BatchTask{first + (int)k, (int16_t)cnt, 0, (int8_t)logn, 0, 0, 0});
+                small_cost.push_back((double)cnt * (double)(int64_t(1) << logn));
+            }
+        }
+    }
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return MOA_ERR_CUDA;
+    const int64_t resident = (int64_t)sms * moa::batched_blocks_per_sm();
+
+    // Queue: the column tiles of the large transforms in order; each
+    // transform's row tiles follow its last column tile about one wave of
+    // blocks later (so its workspace is still in L2 when read back and the
+    // row tiles rarely wait); then the small tasks, longest first.
+    std::vector<moa::BatchTask> queue;
+    {
+        struct Pending {
+            size_t idx;
+            int64_t ready_at;
+        };
+        std::vector<Pending> pending;
+        size_t next_pending = 0;
+        int64_t emitted_cols = 0;
+        auto emit_rows = [&](size_t li) {
+            const int logn = large_logn[li], lr = batched_logr(logn);
+            for (int g = 0; g < (1 << (logn - 12)); ++g)
+                queue.push_back(moa::BatchTask{large[li], 1, (int16_t)g, (int8_t)logn, (int8_t)lr, 2, 0});
+        };
+        for (size_t li = 0; li < large.size(); ++li) {
+            const int logn = large_logn[li], lr = batched_logr(logn);
+            for (int g = 0; g < (1 << (logn - 12)); ++g) {
+                queue.push_back(moa::BatchTask{large[li], 1, (int16_t)g, (int8_t)logn, (int8_t)lr, 1, 0});
+                ++emitted_cols;
+                while (next_pending < pending.size() && pending[next_pending].ready_at <= emitted_cols)
+                    emit_rows(pending[next_pending++].idx);
+            }
+            pending.push_back(Pending{li, emitted_cols + resident});
+        }
+        while (next_pending < pending.size())
+            emit_rows(pending[next_pending++].idx);
+        std::vector<size_t> order(small.size());
+        for (size_t i = 0; i < order.size(); ++i)
+            order[i] = i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](size_t a, size_t b) { return small_cost[a] > small_cost[b]; });
+        for (size_t i : order)
+            queue.push_back(small[i]);
+    }
+
+    // device block: status | tasks | offsets | ticket | tables struct | stage tables | two-level tables
+    auto align = [](size_t v) { return (v + 255) & ~size_t(255); };
+    size_t bytes = 256;
+    const size_t tasks_off = bytes;
+    bytes = align(bytes + queue.size() * sizeof(moa::BatchTask));
+    const size_t offs_off = bytes;
+    bytes = align(bytes + offs_sorted.size() * sizeof(int64_t));
+    const size_t ticket_off = bytes;   // ticket, then one completion counter per transform
+    bytes = align(bytes + sizeof(int) * (size_t)(1 + count));
+    const size_t tables_off = bytes;
+    bytes = align(bytes + sizeof(moa::BatchTables));
+    size_t stage_off[13] = {0}, lo_off[17] = {0}, hi_off[17] = {0};
+    for (int l = 1; l <= 12; ++l)
+        if (need_stage[l] && moa::stage_table_entries(l) > 0) {
+            stage_off[l] = bytes;
+            bytes = align(bytes + (size_t)moa::stage_table_entries(l) * sizeof(float2));
+        }
+    for (int l = 13; l <= 16; ++l)
+        if (need_lift[l]) {
+            const int h = (l + 1) / 2;
+            lo_off[l] = bytes;
+            bytes = align(bytes + (size_t(1) << h) * sizeof(float2));
+            hi_off[l] = bytes;
+            bytes = align(bytes + (size_t(1) << (l - h)) * sizeof(float2));
+        }
+    void *blk = nullptr;
+    if (dev_alloc(&blk, bytes) != cudaSuccess)
+        return MOA_ERR_ALLOC;
+    p->batch_block = blk;
+    if (!large.empty()) {
+        void *ws = nullptr;
+        p->workspace_bytes = (size_t)total * sizeof(float2);
+        if (dev_alloc(&ws, p->workspace_bytes) != cudaSuccess)
+            return MOA_ERR_ALLOC;
+        p->workspace = static_cast<float2 *>(ws);
+    }
+    char *base = static_cast<char *>(blk);
+    p->d_status = reinterpret_cast<int *>(base);
+    if (moa::prepare_kernels() != cudaSuccess)
+        return MOA_ERR_CUDA;
+    moa::BatchTables tb{};
+    for (int l = 1; l <= 12; ++l)
+        if (stage_off[l]) {
+            float2 *t = reinterpret_cast<float2 *>(base + stage_off[l]);
+            if (moa::generate_stage_table(t, l, 0) != cudaSuccess)
+                return MOA_ERR_CUDA;
+            tb.stage[l] = t;
+        }
+    for (int l = 13; l <= 16; ++l)
+        if (need_lift[l]) {
+            float2 *lo = reinterpret_cast<float2 *>(base + lo_off[l]);
+            float2 *hi = reinterpret_cast<float2 *>(base + hi_off[l]);
+            if (moa::generate_two_level(lo, hi, l, (l + 1) / 2, 0) != cudaSuccess)
+                return MOA_ERR_CUDA;
+            tb.lo[l] = lo;
+            tb.hi[l] = hi;
+            tb.h[l] = (l + 1) / 2;
+        }
+    if (cudaMemset(base, 0, 256) != cudaSuccess ||
+        cudaMemcpy(base + tasks_off, queue.data(), queue.size() * sizeof(moa::BatchTask), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(base + offs_off, offs_sorted.data(), offs_sorted.size() * sizeof(int64_t),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(base + tables_off, &tb, sizeof(tb), cudaMemcpyHostToDevice) != cudaSuccess)
+        return MOA_ERR_CUDA;
+    p->bl.tasks = reinterpret_cast<const moa::BatchTask *>(base + tasks_off);
+    p->bl.ntasks = (int)queue.size();
+    p->bl.ticket = reinterpret_cast<int *>(base + ticket_off);
+    p->bl.ncounters = (int)count;
+    p->bl.offs = reinterpret_cast<const int64_t *>(base + offs_off);
+    p->bl.ws = p->workspace;
+    p->bl.tables = reinterpret_cast<const moa::BatchTables *>(base + tables_off);
+    const int64_t grid = std::min<int64_t>(resident, (int64_t)queue.size());
+    p->bl.grid = (unsigned)std::max<int64_t>(grid, 1);
+    if (cudaDeviceSynchronize() != cudaSuccess)
+        return MOA_ERR_CUDA;
+    return MOA_OK;
+}
+
 moa_status_t run_pass(moa_fft_plan_s *p, size_t i, const void *in, void *out, cudaStream_t s, int sign)
 {
+    if (p->batched) {
+        const int flags = sign > 0 ? (moa::FLAG_CONJ_IN | moa::FLAG_CONJ_OUT) : 0;
+        return moa::launch_batched(p->bl, static_cast<const float2 *>(in), static_cast<float2 *>(out), flags, s,
+                                   p->d_status) == cudaSuccess
+                   ? MOA_OK
+                   : MOA_ERR_CUDA;
+    }
     const PassDesc &d = p->passes[i];
     const size_t np = p->passes.size();
     auto buf = [&](int id) -> float2 * {
@@ -322,7 +527,8 @@ moa_status_t run(moa_fft_plan_s *p, const void *in, void *out, void *stream, int
     if (st != MOA_OK)
         return st;
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
-    for (size_t i = 0; i < p->passes.size(); ++i)
+    const size_t np = p->batched ? 1 : p->passes.size();
+    for (size_t i = 0; i < np; ++i)
         if ((st = run_pass(p, i, in, out, s, sign)) != MOA_OK)
             return st;
     return MOA_OK;
@@ -390,10 +596,35 @@ moa_status_t moa_fft_plan_batched(moa_fft_plan_t *plan, const int64_t *lengths, 
         return MOA_ERR_INVALID_ARG;
     if (dtype != MOA_C64 && dtype != MOA_C64_TC_FP16 && dtype != MOA_C64_TC_BF16)
         return MOA_ERR_INVALID_ARG;
-    for (int64_t i = 0; i < count; ++i)
+    int64_t total = 0;
+    for (int64_t i = 0; i < count; ++i) {
         if (!pow2_ge2(lengths[i]))
             return MOA_ERR_INVALID_SIZE;
-    return MOA_ERR_UNSUPPORTED;
+        if (lengths[i] > 65536)
+            return MOA_ERR_UNSUPPORTED;
+        total += lengths[i];
+        if (total >= (int64_t(1) << 31))
+            return MOA_ERR_UNSUPPORTED;
+    }
+    if (dtype != MOA_C64)
+        return MOA_ERR_UNSUPPORTED;
+    moa_fft_plan_s *p = new (std::nothrow) moa_fft_plan_s();
+    if (!p)
+        return MOA_ERR_ALLOC;
+    p->sign = sign;
+    p->dtype = dtype;
+    moa_status_t st = build_batched(p, lengths, count);
+    if (st != MOA_OK) {
+        free_plan_memory(p);
+        delete p;
+        return st;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_plans_mu);
+        g_plans.insert(p);
+    }
+    *plan = p;
+    return MOA_OK;
 }
 
 moa_status_t moa_fft_exec(moa_fft_plan_t plan, const void *in, void *out, void *stream)
@@ -415,7 +646,7 @@ moa_status_t moa_fft_exec_pass(moa_fft_plan_t plan, int index, int sign, const v
 {
     if (!is_live(plan) || (sign != 1 && sign != -1))
         return MOA_ERR_INVALID_ARG;
-    if (index < 0 || (size_t)index >= plan->passes.size())
+    if (index < 0 || (size_t)index >= (plan->batched ? 1 : plan->passes.size()))
         return MOA_ERR_INVALID_ARG;
     moa_status_t st = check_io(in, out);
     if (st != MOA_OK)
@@ -474,7 +705,7 @@ moa_status_t moa_fft_plan_info(moa_fft_plan_t plan, int *passes, int64_t *split_
     if (!is_live(plan))
         return MOA_ERR_INVALID_ARG;
     if (passes)
-        *passes = (int)plan->passes.size();
+        *passes = plan->batched ? 1 : (int)plan->passes.size();
     if (split_r)
         *split_r = plan->split_r;
     if (split_c)
@@ -486,13 +717,15 @@ moa_status_t moa_fft_plan_info(moa_fft_plan_t plan, int *passes, int64_t *split_
 
 moa_status_t moa_fft_pass_info(moa_fft_plan_t plan, int index, char *name, size_t name_len, int64_t *bytes)
 {
-    if (!is_live(plan) || index < 0 || (size_t)index >= plan->passes.size())
+    if (!is_live(plan) || index < 0 || (size_t)index >= (plan->batched ? 1 : plan->passes.size()))
         return MOA_ERR_INVALID_ARG;
     if (name_len > 0 && !name)
         return MOA_ERR_INVALID_ARG;
-    const PassDesc &d = plan->passes[index];
     char buf[64];
-    if (d.pipe)
+    const PassDesc d = plan->batched ? PassDesc{} : plan->passes[index];
+    if (plan->batched)
+        snprintf(buf, sizeof(buf), "batched_kernel");
+    else if (d.pipe)
         snprintf(buf, sizeof(buf), d.kind == moa::PASS_COL ? "pipe_col_kernel<%d,%d>" : "pipe_rowT_kernel<%d>",
                  d.logN, d.tw4);
     else if (d.kind == moa::PASS_COL)

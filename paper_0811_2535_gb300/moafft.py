@@ -173,6 +173,29 @@ class Plan:
             pass
 
 
+class BatchedPlan(Plan):
+    """Independent 1-D transforms of uneven power-of-two lengths (each in
+    [2, 65536]) in one persistent launch.  Transform i occupies the
+    contiguous block starting at sum(lengths[:i]) of the input and output."""
+
+    def __init__(self, lengths: Sequence[int], sign: int = -1, dtype: int = MOA_C64):
+        lengths = [int(n) for n in lengths]
+        self.lengths = tuple(lengths)
+        self.shape, self.batch, self.sign, self.dtype = (sum(lengths),), 1, int(sign), int(dtype)
+        arr = (_I64 * len(lengths))(*lengths)
+        h = _P()
+        _check(lib().moa_fft_plan_batched(ctypes.byref(h), arr, len(lengths), self.sign, self.dtype),
+               f"moa_fft_plan_batched({len(lengths)} transforms)")
+        self._h = h
+
+    def offsets(self):
+        out, acc = [], 0
+        for n in self.lengths:
+            out.append(acc)
+            acc += n
+        return out
+
+
 _plan_cache: dict = {}
 
 

@@ -84,6 +84,8 @@ def test_batched_plan_validation(L):
     assert L.moa_fft_plan_batched(ctypes.byref(h), lens, 3, -1, 0) == 2
     assert L.moa_fft_plan_batched(ctypes.byref(h), lens, 0, -1, 0) == 1
     assert L.moa_fft_plan_batched(None, lens, 3, -1, 0) == 1
+    big = (ctypes.c_int64 * 2)(64, 1 << 17)
+    assert L.moa_fft_plan_batched(ctypes.byref(h), big, 2, -1, 0) == 3      # beyond 2^16: unsupported
 
 
 def test_dead_handles_and_null(L):
