@@ -18,7 +18,13 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <cmath>
+#include <fstream>
+#include <map>
 #include <mutex>
+#include <string>
+#include <sys/stat.h>
+#include <unistd.h>
 #include <set>
 #include <vector>
 
@@ -43,6 +49,10 @@ struct moa_fft_plan_s {
     float2 *workspace = nullptr;
     size_t workspace_bytes = 0;
     int *d_status = nullptr;
+    // choices an autotuner (or an override) may fix: -1 / 0 = default
+    int opt_lr = -1;              // log2 r of a lifted 1-D transform
+    int opt_pipe = -1;            // 0: generic kernels only, 1: pipelined strided kernels allowed
+    int opt_batch_dlr = 0;        // batched: log2 r offset from floor(log2 n / 2)
     // batched plans (moa_fft_plan_batched): one persistent launch
     bool batched = false;
     moa::BatchLaunch bl{};
@@ -191,7 +201,7 @@ moa_status_t build_passes(moa_fft_plan_s *p)
             p->passes.push_back(row_pass(L, B, 1, BUF_IN, BUF_OUT));
             return MOA_OK;
         }
-        int lr = env_int("MOA_SPLIT_LOG2R", L / 2);
+        int lr = p->opt_lr >= 0 ? p->opt_lr : env_int("MOA_SPLIT_LOG2R", L / 2);
         if (lr < 1 || lr > 12 || L - lr < 1 || L - lr > 12)
             lr = L / 2;
         const int lc = L - lr;
@@ -265,7 +275,8 @@ moa_status_t allocate_and_fill(moa_fft_plan_s *p)
     // the pipelined strided kernels need the tensor-map encoder; without it
     // the plan keeps the generic kernels (same results, slower)
     // MOA_PIPE=0 forces the generic kernels (tests compare both paths)
-    const int pipe_mode = moa::pipe_supported() ? env_int("MOA_PIPE", 1) : 0;
+    const int pipe_mode =
+        moa::pipe_supported() ? (p->opt_pipe >= 0 ? p->opt_pipe : env_int("MOA_PIPE", 1)) : 0;
     for (PassDesc &d : p->passes) {
         const bool strided4 = d.logN >= 10 && d.logN <= 12 && d.logF == 2 &&
                               (d.kind == moa::PASS_COL ? d.C >= 4 : d.Rt > 1);
@@ -309,12 +320,13 @@ moa_status_t check_io(const void *in, const void *out)
 // Split of a large transform (2^13..2^16 points) handled inside one block:
 // both factors in [16, 1024] (so every tile holds at least four transforms);
 // default r = 2^floor(log n / 2), MOA_BATCH_LOG2R overrides within range.
-int batched_logr(int logn)
+int batched_logr(int logn, int dlr)
 {
     const int lo = std::max(4, logn - 10), hi = std::min(10, logn - 4);
-    int lr = env_int("MOA_BATCH_LOG2R", logn / 2);
+    const int dflt = std::min(std::max(logn / 2 + dlr, lo), hi);
+    int lr = env_int("MOA_BATCH_LOG2R", dflt);
     if (lr < lo || lr > hi)
-        lr = std::min(std::max(logn / 2, lo), hi);
+        lr = dflt;
     return lr;
 }
 
@@ -350,7 +362,7 @@ moa_status_t build_batched(moa_fft_plan_s *p, const int64_t *lengths, int64_t co
         const int first = (int)offs_sorted.size();
         offs_sorted.insert(offs_sorted.end(), group.begin(), group.end());
         if (logn >= 13) {
-            const int lr = batched_logr(logn);
+            const int lr = batched_logr(logn, p->opt_batch_dlr);
             need_stage[lr] = need_stage[logn - lr] = true;
             need_lift[logn] = true;
             for (size_t k = 0; k < group.size(); ++k) {
@@ -387,12 +399,12 @@ moa_status_t build_batched(moa_fft_plan_s *p, const int64_t *lengths, int64_t co
         size_t next_pending = 0;
         int64_t emitted_cols = 0;
         auto emit_rows = [&](size_t li) {
-            const int logn = large_logn[li], lr = batched_logr(logn);
+            const int logn = large_logn[li], lr = batched_logr(logn, p->opt_batch_dlr);
             for (int g = 0; g < (1 << (logn - 12)); ++g)
                 queue.push_back(moa::BatchTask{large[li], 1, (int16_t)g, (int8_t)logn, (int8_t)lr, 2, 0});
         };
         for (size_t li = 0; li < large.size(); ++li) {
-            const int logn = large_logn[li], lr = batched_logr(logn);
+            const int logn = large_logn[li], lr = batched_logr(logn, p->opt_batch_dlr);
             for (int g = 0; g < (1 << (logn - 12)); ++g) {
                 queue.push_back(moa::BatchTask{large[li], 1, (int16_t)g, (int8_t)logn, (int8_t)lr, 1, 0});
                 ++emitted_cols;
@@ -519,6 +531,147 @@ moa_status_t run_pass(moa_fft_plan_s *p, size_t i, const void *in, void *out, cu
     return MOA_OK;
 }
 
+moa_status_t run_unchecked(moa_fft_plan_s *p, const void *in, void *out, cudaStream_t s, int sign)
+{
+    const size_t np = p->batched ? 1 : p->passes.size();
+    for (size_t i = 0; i < np; ++i) {
+        const moa_status_t st = run_pass(p, i, in, out, s, sign);
+        if (st != MOA_OK)
+            return st;
+    }
+    return MOA_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Autotuner.  The paper leaves the blocking (breakpoint) to the user and
+// proposes a script-based search over alternatives (Sec. 4.8, Sec. 8); the
+// plan does that search itself.  For a lifted 1-D transform it times every
+// valid r x c split with and without the pipelined strided kernels; for a
+// batched plan, three split policies for its large transforms.  Results are
+// kept per process and in a small text cache (MOA_TUNE_CACHE, default
+// $HOME/.cache/moafft/tune.txt) keyed by GPU name.  MOA_AUTOTUNE=0 keeps
+// the defaults; an explicit MOA_SPLIT_LOG2R / MOA_PIPE / MOA_BATCH_LOG2R
+// override also skips the search.
+
+std::mutex g_tune_mu;
+std::map<std::string, std::string> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_path()
+{
+    const char *e = std::getenv("MOA_TUNE_CACHE");
+    if (e && *e)
+        return e;
+    const char *h = std::getenv("HOME");
+    return std::string(h && *h ? h : "/tmp") + "/.cache/moafft/tune.txt";
+}
+
+void tune_load_locked()
+{
+    if (g_tune_loaded)
+        return;
+    g_tune_loaded = true;
+    std::ifstream f(tune_path());
+    std::string key, value;
+    while (f >> key && std::getline(f, value)) {
+        const size_t b = value.find_first_not_of(' ');
+        g_tune[key] = b == std::string::npos ? "" : value.substr(b);
+    }
+}
+
+bool tune_get(const std::string &key, std::string &value)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune.find(key);
+    if (it == g_tune.end())
+        return false;
+    value = it->second;
+    return true;
+}
+
+void tune_put(const std::string &key, const std::string &value)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    g_tune[key] = value;
+    const std::string path = tune_path();
+    const size_t slash = path.rfind('/');
+    if (slash != std::string::npos) {   // create up to two missing directory levels
+        const std::string dir = path.substr(0, slash);
+        const size_t s2 = dir.rfind('/');
+        if (s2 != std::string::npos)
+            mkdir(dir.substr(0, s2).c_str(), 0755);
+        mkdir(dir.c_str(), 0755);
+    }
+    const std::string tmp = path + ".tmp" + std::to_string((long)getpid());
+    {
+        std::ofstream f(tmp);
+        if (!f)
+            return;
+        for (const auto &kv : g_tune)
+            f << kv.first << ' ' << kv.second << '\n';
+    }
+    std::rename(tmp.c_str(), path.c_str());
+}
+
+std::string device_tag()
+{
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+        return "unknown";
+    std::string t = prop.name;
+    for (char &ch : t)
+        if (ch == ' ')
+            ch = '_';
+    return t;
+}
+
+// Mean time of one exec on scratch buffers (zeros); +inf on any failure.
+float time_exec(moa_fft_plan_s *p)
+{
+    const size_t bytes = (size_t)p->total * sizeof(float2);
+    void *a = nullptr, *b = nullptr;
+    if (dev_alloc(&a, bytes) != cudaSuccess)
+        return INFINITY;
+    if (dev_alloc(&b, bytes) != cudaSuccess) {
+        cudaFree(a);
+        return INFINITY;
+    }
+    float ms = INFINITY;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMemset(a, 0, bytes) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
+        cudaEventCreate(&e1) == cudaSuccess) {
+        bool ok = true;
+        for (int i = 0; i < 2 && ok; ++i)
+            ok = run_unchecked(p, a, b, 0, -1) == MOA_OK;
+        const int reps = 5;
+        ok = ok && cudaEventRecord(e0, 0) == cudaSuccess;
+        for (int i = 0; i < reps && ok; ++i)
+            ok = run_unchecked(p, a, b, 0, -1) == MOA_OK;
+        ok = ok && cudaEventRecord(e1, 0) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+        float t = 0.f;
+        if (ok && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
+            ms = t / reps;
+    }
+    if (e0)
+        cudaEventDestroy(e0);
+    if (e1)
+        cudaEventDestroy(e1);
+    cudaFree(a);
+    cudaFree(b);
+    return ms;
+}
+
+bool autotune_enabled() { return env_int("MOA_AUTOTUNE", 1) != 0; }
+bool env_set(const char *name)
+{
+    const char *v = std::getenv(name);
+    return v && *v;
+}
+
 moa_status_t run(moa_fft_plan_s *p, const void *in, void *out, void *stream, int sign)
 {
     if (!is_live(p))
@@ -531,6 +684,56 @@ moa_status_t run(moa_fft_plan_s *p, const void *in, void *out, void *stream, int
     for (size_t i = 0; i < np; ++i)
         if ((st = run_pass(p, i, in, out, s, sign)) != MOA_OK)
             return st;
+    return MOA_OK;
+}
+
+
+// Build a plan (not yet registered) with optional fixed choices.
+moa_status_t make_plan(moa_fft_plan_s **out, const int64_t *n, int dims, int64_t batch, int sign, int dtype,
+                       int64_t total, int opt_lr, int opt_pipe)
+{
+    *out = nullptr;
+    moa_fft_plan_s *p = new (std::nothrow) moa_fft_plan_s();
+    if (!p)
+        return MOA_ERR_ALLOC;
+    p->dims = dims;
+    for (int i = 0; i < dims; ++i)
+        p->n[i] = n[i];
+    p->batch = batch;
+    p->sign = sign;
+    p->dtype = dtype;
+    p->total = total;
+    p->opt_lr = opt_lr;
+    p->opt_pipe = opt_pipe;
+    moa_status_t st = build_passes(p);
+    if (st == MOA_OK)
+        st = allocate_and_fill(p);
+    if (st != MOA_OK) {
+        free_plan_memory(p);
+        delete p;
+        return st;
+    }
+    *out = p;
+    return MOA_OK;
+}
+
+moa_status_t make_batched(moa_fft_plan_s **out, const int64_t *lengths, int64_t count, int sign, int dtype,
+                          int dlr)
+{
+    *out = nullptr;
+    moa_fft_plan_s *p = new (std::nothrow) moa_fft_plan_s();
+    if (!p)
+        return MOA_ERR_ALLOC;
+    p->sign = sign;
+    p->dtype = dtype;
+    p->opt_batch_dlr = dlr;
+    const moa_status_t st = build_batched(p, lengths, count);
+    if (st != MOA_OK) {
+        free_plan_memory(p);
+        delete p;
+        return st;
+    }
+    *out = p;
     return MOA_OK;
 }
 
@@ -560,24 +763,44 @@ moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int6
     if (dtype != MOA_C64)
         return MOA_ERR_UNSUPPORTED;
 
-    moa_fft_plan_s *p = new (std::nothrow) moa_fft_plan_s();
-    if (!p)
-        return MOA_ERR_ALLOC;
-    p->dims = dims;
-    for (int i = 0; i < dims; ++i)
-        p->n[i] = n[i];
-    p->batch = batch;
-    p->sign = sign;
-    p->dtype = dtype;
-    p->total = total;
-    moa_status_t st = build_passes(p);
-    if (st == MOA_OK)
-        st = allocate_and_fill(p);
-    if (st != MOA_OK) {
-        free_plan_memory(p);
-        delete p;
-        return st;
+    int opt_lr = -1, opt_pipe = -1;
+    const int L = ilog2(n[0]);
+    if (dims == 1 && L > 12 && autotune_enabled() && !env_set("MOA_SPLIT_LOG2R")) {
+        const std::string key = device_tag() + ":1d:" + std::to_string(L) + ":" + std::to_string(batch);
+        std::string v;
+        if (tune_get(key, v) && sscanf(v.c_str(), "%d %d", &opt_lr, &opt_pipe) == 2) {
+            // cached choice
+        } else {
+            float best = INFINITY;
+            const bool try_generic = !env_set("MOA_PIPE");
+            for (int lr = std::max(1, L - 12); lr <= std::min(12, L - 1); ++lr) {
+                for (int pipe = 1; pipe >= (try_generic ? 0 : 1); --pipe) {
+                    moa_fft_plan_s *cand = nullptr;
+                    const moa_status_t st = make_plan(&cand, n, dims, batch, sign, dtype, total, lr, try_generic ? pipe : -1);
+                    if (st != MOA_OK)
+                        return st;
+                    const float ms = time_exec(cand);
+                    const bool used_pipe = std::any_of(cand->passes.begin(), cand->passes.end(),
+                                                       [](const PassDesc &d) { return d.pipe != 0; });
+                    free_plan_memory(cand);
+                    delete cand;
+                    if (ms < best) {
+                        best = ms;
+                        opt_lr = lr;
+                        opt_pipe = try_generic ? pipe : -1;
+                    }
+                    if (!used_pipe)
+                        break;   // no pass of this split has a pipelined form
+                }
+            }
+            if (std::isfinite(best))
+                tune_put(key, std::to_string(opt_lr) + " " + std::to_string(opt_pipe));
+        }
     }
+    moa_fft_plan_s *p = nullptr;
+    const moa_status_t st = make_plan(&p, n, dims, batch, sign, dtype, total, opt_lr, opt_pipe);
+    if (st != MOA_OK)
+        return st;
     {
         std::lock_guard<std::mutex> lk(g_plans_mu);
         g_plans.insert(p);
@@ -608,17 +831,41 @@ moa_status_t moa_fft_plan_batched(moa_fft_plan_t *plan, const int64_t *lengths, 
     }
     if (dtype != MOA_C64)
         return MOA_ERR_UNSUPPORTED;
-    moa_fft_plan_s *p = new (std::nothrow) moa_fft_plan_s();
-    if (!p)
-        return MOA_ERR_ALLOC;
-    p->sign = sign;
-    p->dtype = dtype;
-    moa_status_t st = build_batched(p, lengths, count);
-    if (st != MOA_OK) {
-        free_plan_memory(p);
-        delete p;
-        return st;
+    int dlr = 0;
+    bool any_large = false;
+    int hist[17] = {0};
+    for (int64_t i = 0; i < count; ++i) {
+        hist[ilog2(lengths[i])]++;
+        any_large |= lengths[i] > 4096;
     }
+    if (any_large && autotune_enabled() && !env_set("MOA_BATCH_LOG2R")) {
+        std::string key = device_tag() + ":batched:";
+        for (int l = 1; l <= 16; ++l)
+            key += std::to_string(hist[l]) + (l < 16 ? "," : "");
+        std::string v;
+        if (!(tune_get(key, v) && sscanf(v.c_str(), "%d", &dlr) == 1)) {
+            float best = INFINITY;
+            for (int cand_dlr = -1; cand_dlr <= 1; ++cand_dlr) {
+                moa_fft_plan_s *cand = nullptr;
+                const moa_status_t st = make_batched(&cand, lengths, count, sign, dtype, cand_dlr);
+                if (st != MOA_OK)
+                    return st;
+                const float ms = time_exec(cand);
+                free_plan_memory(cand);
+                delete cand;
+                if (ms < best) {
+                    best = ms;
+                    dlr = cand_dlr;
+                }
+            }
+            if (std::isfinite(best))
+                tune_put(key, std::to_string(dlr));
+        }
+    }
+    moa_fft_plan_s *p = nullptr;
+    const moa_status_t st = make_batched(&p, lengths, count, sign, dtype, dlr);
+    if (st != MOA_OK)
+        return st;
     {
         std::lock_guard<std::mutex> lk(g_plans_mu);
         g_plans.insert(p);

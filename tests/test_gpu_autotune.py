@@ -1,0 +1,76 @@
+"""Plan-time autotuner (GPU): it times the admissible r x c splits of a
+lifted 1-D transform (and the split policy of a batched plan), keeps the
+fastest, records the choice in its cache file and reuses it; results stay
+within the parity tolerance whatever it picks."""
+import os
+import time
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-6
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0811_2535_gb300 import build, moafft
+    build.build()
+    import oracle
+    oracle.build()
+    return torch, moafft, oracle
+
+
+def test_autotuned_split_is_cached_and_correct(env, tmp_path, monkeypatch):
+    torch, moafft, oracle = env
+    from paper_0811_2535_gb300 import inputs
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("MOA_TUNE_CACHE", str(cache))
+    monkeypatch.setenv("MOA_AUTOTUNE", "1")
+    for k in ("MOA_SPLIT_LOG2R", "MOA_PIPE", "MOA_BATCH_LOG2R"):
+        monkeypatch.delenv(k, raising=False)
+    n = 1 << 19          # a size not planned elsewhere in this process
+    t0 = time.perf_counter()
+    plan = moafft.Plan([n], 3, -1)
+    t_first = time.perf_counter() - t0
+    info = plan.info()
+    text = cache.read_text()
+    line = [ln for ln in text.splitlines() if ":1d:19:3 " in ln]
+    assert len(line) == 1, text
+    lr, pipe = (int(v) for v in line[0].split()[1:3])
+    assert info["split_r"] == 1 << lr and 7 <= lr <= 12
+    x = inputs.uniform((3, n), 77)
+    y = plan.exec(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = oracle.fft_radix2(x.astype(np.complex128), -1)
+    err = np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= TOL
+    plan.destroy()
+    t0 = time.perf_counter()
+    again = moafft.Plan([n], 3, -1)       # served from the cache: no timing runs
+    t_second = time.perf_counter() - t0
+    assert again.info()["split_r"] == info["split_r"]
+    assert t_second < t_first
+    again.destroy()
+
+
+def test_autotuned_batched_plan(env, tmp_path, monkeypatch):
+    torch, moafft, oracle = env
+    from paper_0811_2535_gb300 import inputs
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("MOA_TUNE_CACHE", str(cache))
+    monkeypatch.setenv("MOA_AUTOTUNE", "1")
+    monkeypatch.delenv("MOA_BATCH_LOG2R", raising=False)
+    lengths = [1 << k for k in (14, 9, 16, 13, 6, 15, 12)]
+    vecs = [inputs.uniform(n, 80 + i) for i, n in enumerate(lengths)]
+    plan = moafft.BatchedPlan(lengths, -1)
+    assert ":batched:" in cache.read_text()
+    x = torch.from_numpy(np.concatenate(vecs)).cuda()
+    y = plan.exec(x).cpu().numpy()
+    for o, n, v in zip(plan.offsets(), lengths, vecs):
+        ref = oracle.fft_radix2(v.astype(np.complex128), -1)
+        assert np.linalg.norm(y[o:o + n] - ref) / np.linalg.norm(ref) <= TOL
+    plan.destroy()
