@@ -271,6 +271,52 @@ def batched_report(torch, moafft, inputs, dev, iters):
             "speedup": t_loop / t_batch}
 
 
+def tensor_core_report(torch, moafft, inputs, dev, iters, with_oracle):
+    """Precision workload 16384 x 4096 (U[-1,1) noise plus 5 complex
+    sinusoids of amplitude 10 per row, seed 3): the plain FP32 row kernel against the
+    tensor-core paths (radix-16 DFT blocks as FP16 hi/lo or BF16 hi/mid/lo
+    products with FP32 accumulation).  Errors: relative L2 per row against
+    the FP64 oracle on 32 sampled rows (oracle leg only)."""
+    import numpy as np
+    n, batch = 4096, 16384
+    x_h = inputs.sinusoids(batch, n, inputs.SEED_PRECISION)
+    x = torch.from_numpy(x_h).to(dev)
+    out = torch.empty_like(x)
+    stream = torch.cuda.current_stream(dev)
+    rows = np.random.default_rng(5).choice(batch, 32, replace=False)
+    ref = None
+    if with_oracle:
+        import oracle
+        ref = oracle.fft_radix2(x_h[rows].astype(np.complex128), -1)
+    alg = 16.0 * n * batch
+    rep = {"workload": "16384 x 1-D 4096, U[-1,1) + 5 sinusoids amp 10 (seed 3), complex64 forward"}
+    for name, dt in (("fp32", 0), ("tc_fp16", 1), ("tc_bf16", 2)):
+        p = moafft.Plan([n], batch, -1, dt)
+        for _ in range(3):
+            p.exec(x, out, stream=stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(iters):
+            p.exec(x, out, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) / iters * 1e3
+        ent = {"kernel": p.pass_info(0)["kernel"], "us": us, "GFLOPs": flops((n,)) * batch / us / 1e3,
+               "algorithmic_GBps": alg / us / 1e3}
+        if ref is not None:
+            y = out.cpu().numpy()[rows].astype(np.complex128)
+            err = np.linalg.norm(y - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
+            ent["rel_l2_max"] = float(err.max())
+            ent["rel_l2_median"] = float(np.median(err))
+        if p.status() != 0:
+            raise RuntimeError("device status word set in the tensor-core report")
+        p.destroy()
+        rep[name] = ent
+    return rep
+
+
 def run_moa(args):
     import numpy as np
     import torch
@@ -404,6 +450,8 @@ def run_moa(args):
         if p.status() != 0:
             raise RuntimeError("device status word set after the benchmark")
     batched = None if args.no_batched else batched_report(torch, moafft, inputs, dev, max(3, min(args.steps, 20)))
+    tensor_core = None if args.no_batched else tensor_core_report(torch, moafft, inputs, dev, max(3, min(args.steps, 20)),
+                                                                  not args.no_oracle)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -412,7 +460,8 @@ def run_moa(args):
                 "config": {"workload": WORKLOAD_NAME, "l2": "inputs larger than L2 (128 MiB each), no flush",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "passes_per_step": launches_per_step},
-                "roofline": roofline, "lifted_1d": lifted, "batched_uneven": batched, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
+                "roofline": roofline, "lifted_1d": lifted, "batched_uneven": batched,
+                "tensor_core": tensor_core, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches_per_step * args.steps, "rel_l2": parity or None,
                 "parity_ok": (all(v <= TOL for v in parity.values()) if parity else None), "kernels": kernels}
         print(json.dumps(line), flush=True)
@@ -428,7 +477,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["moa", "reference"], default="moa")
     ap.add_argument("--no-oracle", action="store_true", help="skip the CPU oracle parity/baseline leg")
-    ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch comparison")
+    ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch and tensor-core comparisons")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -57,8 +57,10 @@ typedef struct moa_fft_plan_s *moa_fft_plan_t;
 
 typedef enum {
     MOA_C64 = 0,          /* plain FP32 complex64 arithmetic */
-    MOA_C64_TC_FP16 = 1,  /* complex64 I/O, radix-16 DFT blocks on FP16 tensor cores (hi/lo split) */
-    MOA_C64_TC_BF16 = 2   /* complex64 I/O, radix-16 DFT blocks on BF16 tensor cores (hi/lo split) */
+    MOA_C64_TC_FP16 = 1,  /* complex64 I/O, radix-16 DFT blocks on FP16 tensor cores: operands split
+                             hi + lo, three products, FP32 accumulate, power-of-two scaling per stage */
+    MOA_C64_TC_BF16 = 2   /* complex64 I/O, radix-16 DFT blocks on BF16 tensor cores: operands split
+                             hi + mid + lo, six products, FP32 accumulate */
 } moa_dtype_t;
 
 typedef enum {
@@ -77,7 +79,10 @@ typedef enum {
  *   dims   : 1, 2 or 3.
  *   batch  : >= 1; batch * prod(n) < 2^31.
  *   sign   : -1 (forward, exp(-2 pi i jk/n)) or +1.
- *   dtype  : a moa_dtype_t value.
+ *   dtype  : a moa_dtype_t value.  MOA_C64: every shape above.  The two
+ *            tensor-core values: 1-D with n[0] = 256 or 4096 (any batch),
+ *            else MOA_ERR_UNSUPPORTED; relative L2 error <= 1e-5 per
+ *            transform against the exact DFT.
  * Builds the pass sequence, generates the twiddle tables in FP64 on the
  * device (rounded once to FP32) and allocates the workspace; synchronises
  * the device once.  On failure *plan is set to NULL. */
@@ -88,7 +93,8 @@ MOA_API moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int di
  * lengths[0..count-1] (each a power of two in [2, 65536]).  Transform i
  * reads and writes the contiguous block starting at element
  * sum_{j<i} lengths[j] of `in` / `out`.  All transforms run in one
- * persistent launch fed by a device work queue. */
+ * persistent launch fed by a device work queue.  dtype must be MOA_C64
+ * (the tensor-core values give MOA_ERR_UNSUPPORTED). */
 MOA_API moa_status_t moa_fft_plan_batched(moa_fft_plan_t *plan, const int64_t *lengths, int64_t count,
                                   int sign, int dtype);
 

@@ -6,7 +6,7 @@
 
 namespace moa {
 
-enum PassKind { PASS_ROW = 0, PASS_COL = 1 };
+enum PassKind { PASS_ROW = 0, PASS_COL = 1, PASS_TC = 2 };
 
 enum PassFlags {
     FLAG_CONJ_IN = 1,    // conjugate on load (sign +1 via conj(F_-(conj x)))
@@ -36,6 +36,7 @@ struct TwiddleSet {
     const float2 *stage[13];   // per logN: stage tables (Sched<logN> layout), or null
     const float2 *lo, *hi;     // two-level table of w_n^e: lo[e & (2^h-1)] * hi[e >> h]
     int h;
+    const float2 *tc;          // tensor-core path: per-stage full tables
 };
 
 // Launch one pass.  `flags` carries FLAG_CONJ_*; FLAG_TW4 is derived from d.
@@ -49,6 +50,14 @@ bool pipe_supported();
 cudaError_t prepare_pipe_kernels();
 cudaError_t launch_pipe_pass(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
                              cudaStream_t stream, int *status);
+// Tensor-core rows (tc_kernels.cu): 1-D transforms of N = 256 or 4096 along
+// contiguous rows, radix-16 blocks as FP16 (hi/lo) or BF16 (hi/mid/lo) GEMMs.
+// `tw` holds the per-stage tables w_M^(u*k), k < 16 (tc_table_entries).
+int tc_table_entries(int logN);
+cudaError_t launch_tc_pass(const PassDesc &d, bool bf16, const float2 *in, float2 *out, const float2 *tw, int flags,
+                           cudaStream_t stream);
+// dst[k*M1 + u] = w_M^(u*k mod M), k < 16, u < M1 (sign -1).
+cudaError_t generate_full_stage(float2 *dst, int64_t M, int64_t M1, cudaStream_t stream);
 // Shared memory bytes and threads per block of a pass.
 size_t pass_smem_bytes(const PassDesc &d);
 int pass_threads(const PassDesc &d);

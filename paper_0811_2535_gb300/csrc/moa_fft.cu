@@ -194,6 +194,18 @@ void free_plan_memory(moa_fft_plan_s *p)
 moa_status_t build_passes(moa_fft_plan_s *p)
 {
     const int64_t B = p->batch;
+    if (p->dtype != MOA_C64) {
+        PassDesc d{};
+        d.kind = moa::PASS_TC;
+        d.logN = ilog2(p->n[0]);
+        d.O = B;
+        d.C = 1;
+        d.Rt = 1;
+        d.src = BUF_IN;
+        d.dst = BUF_OUT;
+        p->passes.push_back(d);
+        return MOA_OK;
+    }
     if (p->dims == 1) {
         const int64_t n = p->n[0];
         const int L = ilog2(n);
@@ -254,6 +266,11 @@ moa_status_t allocate_and_fill(moa_fft_plan_s *p)
         hi_off = bytes;
         bytes += ((size_t(1) << (logn - h)) * sizeof(float2) + 255) & ~size_t(255);
     }
+    size_t tc_off = 0;
+    if (p->dtype != MOA_C64) {
+        tc_off = bytes;
+        bytes += ((size_t)moa::tc_table_entries(p->passes[0].logN) * sizeof(float2) + 255) & ~size_t(255);
+    }
     void *blk = nullptr;
     if (dev_alloc(&blk, bytes) != cudaSuccess)
         return MOA_ERR_ALLOC;
@@ -291,6 +308,15 @@ moa_status_t allocate_and_fill(moa_fft_plan_s *p)
             if (moa::generate_stage_table(const_cast<float2 *>(p->tw.stage[l]), l, 0) != cudaSuccess)
                 return MOA_ERR_CUDA;
         }
+    }
+    if (tc_off) {
+        float2 *t = reinterpret_cast<float2 *>(base + tc_off);
+        const int L = p->passes[0].logN;
+        if (moa::generate_full_stage(t, int64_t(1) << L, int64_t(1) << (L - 4), 0) != cudaSuccess)
+            return MOA_ERR_CUDA;
+        if (L == 12 && moa::generate_full_stage(t + 16 * 256, 256, 16, 0) != cudaSuccess)
+            return MOA_ERR_CUDA;
+        p->tw.tc = t;
     }
     if (p->split_r > 0) {
         float2 *lo = reinterpret_cast<float2 *>(base + lo_off);
@@ -526,6 +552,11 @@ moa_status_t run_pass(moa_fft_plan_s *p, size_t i, const void *in, void *out, cu
         if (i + 1 == np)
             flags |= moa::FLAG_CONJ_OUT;
     }
+    if (d.kind == moa::PASS_TC)
+        return moa::launch_tc_pass(d, p->dtype == MOA_C64_TC_BF16, buf(d.src), buf(d.dst), p->tw.tc, flags, s) ==
+                       cudaSuccess
+                   ? MOA_OK
+                   : MOA_ERR_CUDA;
     if (moa::launch_pass(d, buf(d.src), buf(d.dst), p->tw, flags, s, p->d_status) != cudaSuccess)
         return MOA_ERR_CUDA;
     return MOA_OK;
@@ -760,7 +791,8 @@ moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int6
         if (total >= (int64_t(1) << 31))
             return MOA_ERR_UNSUPPORTED;
     }
-    if (dtype != MOA_C64)
+    // the tensor-core path covers 1-D transforms of 256 or 4096 points
+    if (dtype != MOA_C64 && !(dims == 1 && (n[0] == 256 || n[0] == 4096)))
         return MOA_ERR_UNSUPPORTED;
 
     int opt_lr = -1, opt_pipe = -1;
@@ -972,6 +1004,8 @@ moa_status_t moa_fft_pass_info(moa_fft_plan_t plan, int index, char *name, size_
     const PassDesc d = plan->batched ? PassDesc{} : plan->passes[index];
     if (plan->batched)
         snprintf(buf, sizeof(buf), "batched_kernel");
+    else if (d.kind == moa::PASS_TC)
+        snprintf(buf, sizeof(buf), "tc_row_kernel<%d,%d>", plan->dtype == MOA_C64_TC_BF16 ? 1 : 0, d.logN);
     else if (d.pipe)
         snprintf(buf, sizeof(buf), d.kind == moa::PASS_COL ? "pipe_col_kernel<%d,%d>" : "pipe_rowT_kernel<%d>",
                  d.logN, d.tw4);

@@ -43,6 +43,18 @@ __global__ void power_table_kernel(float2 *dst, int64_t count, int64_t step, int
     dst[idx] = make_float2((float)c, (float)(-s));
 }
 
+__global__ void full_stage_kernel(float2 *dst, int64_t M, int64_t M1)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 16 * M1)
+        return;
+    const int64_t k = idx / M1, u = idx % M1;
+    const int64_t e = (u * k) % M;
+    double s, c;
+    sincospi(2.0 * (double)e / (double)M, &s, &c);
+    dst[idx] = make_float2((float)c, (float)(-s));
+}
+
 template <int LOGN>
 int entries_typed() { return Sched<LOGN>::tw_entries(); }
 
@@ -99,6 +111,12 @@ cudaError_t generate_stage_table(float2 *dst, int logN, cudaStream_t stream)
     case 12: return gen_typed<12>(dst, stream);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t generate_full_stage(float2 *dst, int64_t M, int64_t M1, cudaStream_t stream)
+{
+    full_stage_kernel<<<(unsigned)((16 * M1 + 255) / 256), 256, 0, stream>>>(dst, M, M1);
+    return cudaGetLastError();
 }
 
 cudaError_t generate_powers(float2 *dst, int64_t count, int64_t step, int64_t modulus, cudaStream_t stream)
