@@ -30,6 +30,8 @@ struct PassDesc {
     int src, dst;   // buffer ids: 0 = user in, 1 = user out, 2 = workspace
     int tw4;        // apply the four-step twiddle (PASS_COL)
     int pipe;       // 1: persistent TMA-pipelined kernel (pipe_kernels.cu)
+    int blk;        // blocked workspace of the lifted transform (pipe kernels only):
+                    // 1 = pass 1 writes 4 x 4 blocks, 2 = pass 2 reads them
 };
 
 struct TwiddleSet {

@@ -292,14 +292,24 @@ moa_status_t allocate_and_fill(moa_fft_plan_s *p)
     // the pipelined strided kernels need the tensor-map encoder; without it
     // the plan keeps the generic kernels (same results, slower)
     // MOA_PIPE=0 forces the generic kernels (tests compare both paths)
+    // MOA_PIPE=1 keeps them but without the blocked workspace
     const int pipe_mode =
-        moa::pipe_supported() ? (p->opt_pipe >= 0 ? p->opt_pipe : env_int("MOA_PIPE", 1)) : 0;
+        moa::pipe_supported() ? (p->opt_pipe >= 0 ? p->opt_pipe : env_int("MOA_PIPE", 2)) : 0;
     for (PassDesc &d : p->passes) {
         const bool strided4 = d.logN >= 10 && d.logN <= 12 && d.logF == 2 &&
                               (d.kind == moa::PASS_COL ? d.C >= 4 : d.Rt > 1);
         d.pipe = 0;
+        d.blk = 0;
         if (strided4 && pipe_mode > 0)
             d.pipe = 1;
+    }
+    // lifted 1-D with both passes pipelined: the intermediate goes through
+    // the workspace as 4 x 4 blocks (whole-block stores in pass 1, whole-block
+    // loads in pass 2 instead of 32-byte segments)
+    if (pipe_mode >= 2 && p->dims == 1 && p->passes.size() == 2 && p->passes[0].pipe && p->passes[1].pipe &&
+        p->passes[0].kind == moa::PASS_COL && p->passes[0].tw4 && p->passes[1].kind == moa::PASS_ROW) {
+        p->passes[0].blk = 1;
+        p->passes[1].blk = 2;
     }
     for (int l = 1; l <= 12; ++l) {
         p->tw.stage[l] = nullptr;
@@ -798,7 +808,7 @@ moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int6
     int opt_lr = -1, opt_pipe = -1;
     const int L = ilog2(n[0]);
     if (dims == 1 && L > 12 && autotune_enabled() && !env_set("MOA_SPLIT_LOG2R")) {
-        const std::string key = device_tag() + ":1d:" + std::to_string(L) + ":" + std::to_string(batch);
+        const std::string key = device_tag() + ":1d2:" + std::to_string(L) + ":" + std::to_string(batch);
         std::string v;
         if (tune_get(key, v) && sscanf(v.c_str(), "%d %d", &opt_lr, &opt_pipe) == 2) {
             // cached choice
@@ -806,11 +816,18 @@ moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int6
             float best = INFINITY;
             const bool try_generic = !env_set("MOA_PIPE");
             for (int lr = std::max(1, L - 12); lr <= std::min(12, L - 1); ++lr) {
-                for (int pipe = 1; pipe >= (try_generic ? 0 : 1); --pipe) {
+                for (int pipe = 2; pipe >= (try_generic ? 0 : 2); --pipe) {
                     moa_fft_plan_s *cand = nullptr;
                     const moa_status_t st = make_plan(&cand, n, dims, batch, sign, dtype, total, lr, try_generic ? pipe : -1);
                     if (st != MOA_OK)
                         return st;
+                    const bool used_blk = std::any_of(cand->passes.begin(), cand->passes.end(),
+                                                      [](const PassDesc &d) { return d.blk != 0; });
+                    if (try_generic && pipe == 2 && !used_blk) {
+                        free_plan_memory(cand);
+                        delete cand;
+                        continue;   // same plan as pipe = 1
+                    }
                     const float ms = time_exec(cand);
                     const bool used_pipe = std::any_of(cand->passes.begin(), cand->passes.end(),
                                                        [](const PassDesc &d) { return d.pipe != 0; });
@@ -1006,9 +1023,10 @@ moa_status_t moa_fft_pass_info(moa_fft_plan_t plan, int index, char *name, size_
         snprintf(buf, sizeof(buf), "batched_kernel");
     else if (d.kind == moa::PASS_TC)
         snprintf(buf, sizeof(buf), "tc_row_kernel<%d,%d>", plan->dtype == MOA_C64_TC_BF16 ? 1 : 0, d.logN);
+    else if (d.pipe && (d.kind == moa::PASS_COL || d.blk == 2))
+        snprintf(buf, sizeof(buf), "pipe_col_kernel<%d,%d,%d>", d.logN, d.tw4, d.blk);
     else if (d.pipe)
-        snprintf(buf, sizeof(buf), d.kind == moa::PASS_COL ? "pipe_col_kernel<%d,%d>" : "pipe_rowT_kernel<%d>",
-                 d.logN, d.tw4);
+        snprintf(buf, sizeof(buf), "pipe_rowT_kernel<%d>", d.logN);
     else if (d.kind == moa::PASS_COL)
         snprintf(buf, sizeof(buf), "col_pass_kernel<%d,%d>", d.logN, d.tw4);
     else

@@ -69,6 +69,15 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
 {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -137,7 +146,19 @@ __device__ __forceinline__ void three_stages(float2 (&v)[16], float2 *E, int tau
 }
 
 // Column pass: view [O][N][C], tile = 4 consecutive columns of one o.
-template <int LOGN, bool TW4>
+//
+// BLK selects the blocked workspace of the lifted transform, in which the
+// r x c intermediate is stored as 4 x 4 blocks of 128 bytes: element
+// (k1, j2) at ((j2/4)*(r/4) + k1/4)*16 + (j2%4)*4 + k1%4.  A tile of four
+// columns then writes whole blocks (256 contiguous bytes per warp) and the
+// tile of four rows of the second pass reads whole blocks.
+//   BLK = 0: rows of the tile from a 2-D tensor map, output in the [O][N][C]
+//            view (32-byte row segments);
+//   BLK = 1: lifted pass 1 (N = r, C = c): 2-D tensor map in, blocked out;
+//   BLK = 2: lifted pass 2 (N = c, C = r): the blocked workspace through a
+//            3-D tensor map {32 floats, r/4, O*c/4}, output in the [O][N][C]
+//            view, i.e. X[k1 + r*k2].
+template <int LOGN, bool TW4, int BLK>
 __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
     pipe_col_kernel(const __grid_constant__ CUtensorMap tmap, float2 *out, int C, int logTpo, int ntiles,
                     const float2 *__restrict__ tw, const float2 *__restrict__ tw_lo, const float2 *__restrict__ tw_hi,
@@ -162,8 +183,12 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
         const int c0 = (tile & tpo_mask) << 2;
         mbar_arrive_expect_tx(b, NH * 4 * (uint32_t)sizeof(float2));
 #pragma unroll
-        for (int k = 0; k < NH / 256; ++k)
-            tma_load_2d(dst + k * 256 * 4, &tmap, b, 2 * c0, o * N + h * NH + k * 256);
+        for (int k = 0; k < NH / 256; ++k) {
+            if constexpr (BLK == 2)
+                tma_load_3d(dst + k * 256 * 4, &tmap, b, 0, c0 >> 2, (o * N + h * NH + k * 256) >> 2);
+            else
+                tma_load_2d(dst + k * 256 * 4, &tmap, b, 2 * c0, o * N + h * NH + k * 256);
+        }
     };
 
     if (tid == 0) {
@@ -234,11 +259,21 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
             for (int k = 0; k < 16; ++k)
                 v[k].y = -v[k].y;
         }
-        float2 *dst = out + (int64_t)o * N * C + col + (int64_t)tau * C;
-        const int64_t step = (int64_t)T * C;
+        if constexpr (BLK == 1) {
+            // element (tau + T*k, col) of the tile: block ((col/4)*(N/4) + (tau + T*k)/4),
+            // slot f*4 + tau%4 (T is a multiple of 4)
+            float2 *dst = out + (int64_t)o * N * C + (int64_t)((col >> 2) * (N >> 2)) * 16 + f * 4 + (tau >> 2) * 16 +
+                          (tau & 3);
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
-            dst[k * step] = v[k];
+            for (int k = 0; k < 16; ++k)
+                dst[k * 4 * T] = v[k];
+        } else {
+            float2 *dst = out + (int64_t)o * N * C + col + (int64_t)tau * C;
+            const int64_t step = (int64_t)T * C;
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                dst[k * step] = v[k];
+        }
     }
 }
 
@@ -371,34 +406,57 @@ template <int LOGN> size_t rowT_smem() { return PipeSmem::bytes<LOGN>(); }
 
 int g_num_sms = 0;
 
+// Column pass over the [O][N][C] view (BLK 0 or 1) or the second pass of the
+// lifted transform over the blocked workspace (BLK 2; O = B, C = r).
 template <int LOGN>
-cudaError_t launch_col(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
-                       cudaStream_t stream, int *status)
+cudaError_t launch_col(const PassDesc &d, int64_t O, int64_t C, int blk, const float2 *in, float2 *out,
+                       const TwiddleSet &tw, int flags, cudaStream_t stream, int *status)
 {
     EncodeTiledFn enc = encode_fn();
     if (!enc)
         return cudaErrorNotSupported;
     CUtensorMap map;
-    const cuuint64_t dims[2] = {(cuuint64_t)(2 * d.C), (cuuint64_t)(d.O << LOGN)};
-    const cuuint64_t strides[1] = {(cuuint64_t)(2 * d.C * sizeof(float))};
-    const cuuint32_t box[2] = {8, 256};
-    const cuuint32_t estr[2] = {1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2 *>(in), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    CUresult r;
+    if (blk == 2) {
+        // {floats of one 4 x 4 block, blocks along k1, blocks along j2 of every o}
+        const cuuint64_t dims[3] = {32, (cuuint64_t)(C >> 2), (cuuint64_t)(O << (LOGN - 2))};
+        const cuuint64_t strides[2] = {128, (cuuint64_t)((C >> 2) * 128)};
+        const cuuint32_t box[3] = {32, 1, 64};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2 *>(in), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        const cuuint64_t dims[2] = {(cuuint64_t)(2 * C), (cuuint64_t)(O << LOGN)};
+        const cuuint64_t strides[1] = {(cuuint64_t)(2 * C * sizeof(float))};
+        const cuuint32_t box[2] = {8, 256};
+        const cuuint32_t estr[2] = {1, 1};
+        r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2 *>(in), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    if (r != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     int logTpo = 0;
-    while ((int64_t(1) << logTpo) < (d.C >> 2))
+    while ((int64_t(1) << logTpo) < (C >> 2))
         ++logTpo;
-    const int ntiles = (int)(d.O << logTpo);
+    const int ntiles = (int)(O << logTpo);
     const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
     const size_t smem = col_smem<LOGN>();
-    if (d.tw4)
-        pipe_col_kernel<LOGN, true><<<grid, 1 << (LOGN - 2), smem, stream>>>(
-            map, out, (int)d.C, logTpo, ntiles, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags, status);
+    const dim3 g(grid), b(1 << (LOGN - 2));
+    const int Ci = (int)C;
+    if (blk == 2)
+        pipe_col_kernel<LOGN, false, 2><<<g, b, smem, stream>>>(map, out, Ci, logTpo, ntiles, tw.stage[LOGN], tw.lo,
+                                                                tw.hi, tw.h, flags, status);
+    else if (d.tw4 && blk == 1)
+        pipe_col_kernel<LOGN, true, 1><<<g, b, smem, stream>>>(map, out, Ci, logTpo, ntiles, tw.stage[LOGN], tw.lo,
+                                                               tw.hi, tw.h, flags, status);
+    else if (d.tw4)
+        pipe_col_kernel<LOGN, true, 0><<<g, b, smem, stream>>>(map, out, Ci, logTpo, ntiles, tw.stage[LOGN], tw.lo,
+                                                               tw.hi, tw.h, flags, status);
     else
-        pipe_col_kernel<LOGN, false><<<grid, 1 << (LOGN - 2), smem, stream>>>(
-            map, out, (int)d.C, logTpo, ntiles, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags, status);
+        pipe_col_kernel<LOGN, false, 0><<<g, b, smem, stream>>>(map, out, Ci, logTpo, ntiles, tw.stage[LOGN], tw.lo,
+                                                                tw.hi, tw.h, flags, status);
     return cudaGetLastError();
 }
 
@@ -417,11 +475,11 @@ template <int LOGN>
 cudaError_t set_pipe_attrs()
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(pipe_col_kernel<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)col_smem<LOGN>())) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(pipe_col_kernel<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)col_smem<LOGN>())) != cudaSuccess)
+    const int cs = (int)col_smem<LOGN>();
+    if ((e = cudaFuncSetAttribute(pipe_col_kernel<LOGN, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) ||
+        (e = cudaFuncSetAttribute(pipe_col_kernel<LOGN, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) ||
+        (e = cudaFuncSetAttribute(pipe_col_kernel<LOGN, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) ||
+        (e = cudaFuncSetAttribute(pipe_col_kernel<LOGN, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs)))
         return e;
     return cudaFuncSetAttribute(pipe_rowT_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)rowT_smem<LOGN>());
@@ -447,11 +505,14 @@ cudaError_t prepare_pipe_kernels()
 cudaError_t launch_pipe_pass(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
                              cudaStream_t stream, int *status)
 {
-    if (d.kind == PASS_COL) {
+    if (d.kind == PASS_COL || d.blk == 2) {
+        // blocked second pass: O = B transforms of the r x c array, C = r columns
+        const int64_t O = d.kind == PASS_COL ? d.O : d.O / d.Rt;
+        const int64_t C = d.kind == PASS_COL ? d.C : d.Rt;
         switch (d.logN) {
-        case 10: return launch_col<10>(d, in, out, tw, flags, stream, status);
-        case 11: return launch_col<11>(d, in, out, tw, flags, stream, status);
-        case 12: return launch_col<12>(d, in, out, tw, flags, stream, status);
+        case 10: return launch_col<10>(d, O, C, d.blk, in, out, tw, flags, stream, status);
+        case 11: return launch_col<11>(d, O, C, d.blk, in, out, tw, flags, stream, status);
+        case 12: return launch_col<12>(d, O, C, d.blk, in, out, tw, flags, stream, status);
         default: return cudaErrorInvalidValue;
         }
     }

@@ -199,10 +199,33 @@ def test_pipelined_and_generic_kernels_agree(env, shape, batch, monkeypatch):
     x = inputs.uniform((batch,) + shape, 6000 + len(shape))
     ref = oracle_ref(env, x, list(shape), batch, -1)
     ys = []
-    for pipe in ("1", "0"):
+    for pipe in ("2", "1", "0"):
         monkeypatch.setenv("MOA_PIPE", pipe)
         for sign in (-1,):
             y, _ = run(env, list(shape), batch, sign, x)
             assert per_transform_rel(y, ref, batch).max() <= TOL, pipe
             ys.append(y)
-    assert per_transform_rel(ys[0], ys[1], batch).max() <= TOL
+    assert per_transform_rel(ys[0], ys[2], batch).max() <= TOL
+    assert per_transform_rel(ys[1], ys[2], batch).max() <= TOL
+
+
+@pytest.mark.parametrize("L,lr,batch", [(24, 12, 1), (22, 11, 2), (20, 10, 3), (23, 12, 1), (23, 11, 2), (21, 10, 1)])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_blocked_workspace_lifted(env, L, lr, batch, sign, monkeypatch):
+    """Lifted 1-D with the intermediate in 4 x 4 blocks: pass 1 is the
+    column kernel with block stores, pass 2 the column kernel reading the
+    blocks through a 3-D tensor map; every r x c split with r, c >= 1024."""
+    torch, moafft, _ = env
+    from paper_0811_2535_gb300 import inputs
+    monkeypatch.setenv("MOA_PIPE", "2")
+    monkeypatch.setenv("MOA_SPLIT_LOG2R", str(lr))
+    n = 1 << L
+    x = inputs.uniform((batch, n), 6100 + L + lr)
+    plan = moafft.Plan([n], batch, sign)
+    names = [plan.pass_info(i)["kernel"] for i in range(plan.info()["passes"])]
+    assert names == ["pipe_col_kernel<%d,1,1>" % lr, "pipe_col_kernel<%d,0,2>" % (L - lr)], names
+    y = plan.exec(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert plan.status() == 0
+    plan.destroy()
+    ref = oracle_ref(env, x, [n], batch, sign)
+    assert per_transform_rel(y, ref, batch).max() <= TOL
