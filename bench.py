@@ -275,7 +275,8 @@ def tensor_core_report(torch, moafft, inputs, dev, iters, with_oracle):
     """Precision workload 16384 x 4096 (U[-1,1) noise plus 5 complex
     sinusoids of amplitude 10 per row, seed 3): the plain FP32 row kernel against the
     tensor-core paths (radix-16 DFT blocks as FP16 hi/lo or BF16 hi/mid/lo
-    products with FP32 accumulation).  Errors: relative L2 per row against
+    products with FP32 accumulation), on tcgen05 and, as the legacy baseline,
+    on mma.sync.  Errors: relative L2 per row against
     the FP64 oracle on 32 sampled rows (oracle leg only)."""
     import numpy as np
     n, batch = 4096, 16384
@@ -290,7 +291,9 @@ def tensor_core_report(torch, moafft, inputs, dev, iters, with_oracle):
         ref = oracle.fft_radix2(x_h[rows].astype(np.complex128), -1)
     alg = 16.0 * n * batch
     rep = {"workload": "16384 x 1-D 4096, U[-1,1) + 5 sinusoids amp 10 (seed 3), complex64 forward"}
-    for name, dt in (("fp32", 0), ("tc_fp16", 1), ("tc_bf16", 2)):
+    for name, dt, kern in (("fp32", 0, ""), ("tc_fp16", 1, ""), ("tc_bf16", 2, ""), ("tc_fp16_mma_sync", 1, "sync"),
+                           ("tc_bf16_mma_sync", 2, "sync")):
+        os.environ["MOA_TC_KERNEL"] = kern
         p = moafft.Plan([n], batch, -1, dt)
         for _ in range(3):
             p.exec(x, out, stream=stream)
@@ -314,6 +317,7 @@ def tensor_core_report(torch, moafft, inputs, dev, iters, with_oracle):
             raise RuntimeError("device status word set in the tensor-core report")
         p.destroy()
         rep[name] = ent
+    os.environ.pop("MOA_TC_KERNEL", None)
     return rep
 
 

@@ -32,6 +32,7 @@ struct PassDesc {
     int pipe;       // 1: persistent TMA-pipelined kernel (pipe_kernels.cu)
     int blk;        // blocked workspace of the lifted transform (pipe kernels only):
                     // 1 = pass 1 writes 4 x 4 blocks, 2 = pass 2 reads them
+    int umma;       // PASS_TC: 1 = tcgen05 kernel (tc_umma.cu), 0 = mma.sync kernel
 };
 
 struct TwiddleSet {
@@ -59,6 +60,11 @@ int tc_table_entries(int logN);
 cudaError_t launch_tc_pass(const PassDesc &d, bool bf16, const float2 *in, float2 *out, const float2 *tw, int flags,
                            cudaStream_t stream);
 // dst[k*M1 + u] = w_M^(u*k mod M), k < 16, u < M1 (sign -1).
+// The same pass on the tcgen05 tensor cores (operands in shared memory,
+// accumulators in tensor memory); `status` receives MOA_ERR_TIMEOUT if a
+// wait for the products gives up.
+cudaError_t launch_umma_pass(const PassDesc &d, bool bf16, const float2 *in, float2 *out, const float2 *tw, int flags,
+                             cudaStream_t stream, int *status);
 cudaError_t generate_full_stage(float2 *dst, int64_t M, int64_t M1, cudaStream_t stream);
 // Shared memory bytes and threads per block of a pass.
 size_t pass_smem_bytes(const PassDesc &d);

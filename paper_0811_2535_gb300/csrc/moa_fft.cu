@@ -203,6 +203,9 @@ moa_status_t build_passes(moa_fft_plan_s *p)
         d.Rt = 1;
         d.src = BUF_IN;
         d.dst = BUF_OUT;
+        // tcgen05 kernel by default; MOA_TC_KERNEL=sync selects the mma.sync one
+        const char *tk = getenv("MOA_TC_KERNEL");
+        d.umma = (tk && strcmp(tk, "sync") == 0) ? 0 : 1;
         p->passes.push_back(d);
         return MOA_OK;
     }
@@ -562,11 +565,13 @@ moa_status_t run_pass(moa_fft_plan_s *p, size_t i, const void *in, void *out, cu
         if (i + 1 == np)
             flags |= moa::FLAG_CONJ_OUT;
     }
-    if (d.kind == moa::PASS_TC)
-        return moa::launch_tc_pass(d, p->dtype == MOA_C64_TC_BF16, buf(d.src), buf(d.dst), p->tw.tc, flags, s) ==
-                       cudaSuccess
-                   ? MOA_OK
-                   : MOA_ERR_CUDA;
+    if (d.kind == moa::PASS_TC) {
+        const bool bf16 = p->dtype == MOA_C64_TC_BF16;
+        const cudaError_t e = d.umma ? moa::launch_umma_pass(d, bf16, buf(d.src), buf(d.dst), p->tw.tc, flags, s,
+                                                             p->d_status)
+                                     : moa::launch_tc_pass(d, bf16, buf(d.src), buf(d.dst), p->tw.tc, flags, s);
+        return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
+    }
     if (moa::launch_pass(d, buf(d.src), buf(d.dst), p->tw, flags, s, p->d_status) != cudaSuccess)
         return MOA_ERR_CUDA;
     return MOA_OK;
@@ -1022,7 +1027,8 @@ moa_status_t moa_fft_pass_info(moa_fft_plan_t plan, int index, char *name, size_
     if (plan->batched)
         snprintf(buf, sizeof(buf), "batched_kernel");
     else if (d.kind == moa::PASS_TC)
-        snprintf(buf, sizeof(buf), "tc_row_kernel<%d,%d>", plan->dtype == MOA_C64_TC_BF16 ? 1 : 0, d.logN);
+        snprintf(buf, sizeof(buf), d.umma ? "tc_umma_kernel<%d,%d>" : "tc_row_kernel<%d,%d>",
+                 plan->dtype == MOA_C64_TC_BF16 ? 1 : 0, d.logN);
     else if (d.pipe && (d.kind == moa::PASS_COL || d.blk == 2))
         snprintf(buf, sizeof(buf), "pipe_col_kernel<%d,%d,%d>", d.logN, d.tw4, d.blk);
     else if (d.pipe)

@@ -19,35 +19,19 @@
 // (persistent over rows): coalesced load to shared memory, three (or two)
 // stages whose fragments are read from and written back to shared memory
 // at their Stockham positions, coalesced store.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-
 #include "fft_core.cuh"
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace moa {
 
 namespace {
 
-// cos(2 pi j / 16), sin(2 pi j / 16), j = 0..15
-__constant__ float c_cos16[16] = {1.f, MOA_C8, MOA_R2, MOA_S8, 0.f, -MOA_S8, -MOA_R2, -MOA_C8,
-                                  -1.f, -MOA_C8, -MOA_R2, -MOA_S8, 0.f, MOA_S8, MOA_R2, MOA_C8};
-__constant__ float c_sin16[16] = {0.f, MOA_S8, MOA_R2, MOA_C8, 1.f, MOA_C8, MOA_R2, MOA_S8,
-                                  0.f, -MOA_S8, -MOA_R2, -MOA_C8, -1.f, -MOA_C8, -MOA_R2, -MOA_S8};
-
 template <bool BF16> struct TC;
 
 template <> struct TC<false> {
     static constexpr int PARTS = 2;
-    // split v into PARTS values whose sum approximates v; packed as raw 16-bit
-    __device__ static void split(float v, uint16_t (&p)[3])
-    {
-        const __half h = __float2half_rn(v);
-        const __half l = __float2half_rn(v - __half2float(h));
-        p[0] = __half_as_ushort(h);
-        p[1] = __half_as_ushort(l);
-        p[2] = 0;
-    }
+    __device__ static void split(float v, uint16_t (&p)[3]) { tc::Split<false>::run(v, p); }
     __device__ static void mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
     {
         asm volatile(
@@ -60,16 +44,7 @@ template <> struct TC<false> {
 
 template <> struct TC<true> {
     static constexpr int PARTS = 3;
-    __device__ static void split(float v, uint16_t (&p)[3])
-    {
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        const float r1 = v - __bfloat162float(h);
-        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-        const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
-        p[0] = __bfloat16_as_ushort(h);
-        p[1] = __bfloat16_as_ushort(m);
-        p[2] = __bfloat16_as_ushort(l);
-    }
+    __device__ static void split(float v, uint16_t (&p)[3]) { tc::Split<true>::run(v, p); }
     __device__ static void mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
     {
         asm volatile(
@@ -80,13 +55,13 @@ template <> struct TC<true> {
     }
 };
 
-__device__ __forceinline__ uint32_t pack(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
+using tc::pack;
 
 // W[row][col] of the 32 x 32 real DFT-16 matrix (sign -1)
 __device__ __forceinline__ float wval(int row, int col)
 {
     const int k = row & 15, m = col & 15, j = (k * m) & 15;
-    const float c = c_cos16[j], s = c_sin16[j];
+    const float c = tc::cos16(j), s = tc::sin16(j);
     if (row < 16)
         return col < 16 ? c : s;     // Re y_k = sum C x_re + S x_im
     return col < 16 ? -s : c;        // Im y_k = sum -S x_re + C x_im
