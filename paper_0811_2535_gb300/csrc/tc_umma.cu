@@ -159,9 +159,11 @@ template <bool BF16> struct TcLayout {
     static constexpr uint32_t EX_BYTES = 256 * RS * 8;     // [256][17] complex64
     static constexpr uint32_t W_PLANE = 2048;              // 32 rows x 32 16-bit entries
     static constexpr uint32_t W_OFF = EX_BYTES;
-    static constexpr uint32_t MISC_OFF = W_OFF + PARTS * W_PLANE;   // mbarrier, TMEM slot, abort flag
+    static constexpr uint32_t TW_OFF = W_OFF + PARTS * W_PLANE;     // stage twiddle table (4096 + 256 complex64)
+    static constexpr uint32_t TW_BYTES = (4096 + 256) * 8;
+    static constexpr uint32_t MISC_OFF = TW_OFF + TW_BYTES;           // mbarrier, TMEM slot, abort flag
     // at most two blocks per SM (their TMEM columns must fit the SM's 512)
-    static constexpr uint32_t BYTES = 80 * 1024;
+    static constexpr uint32_t BYTES = 84 * 1024;
     static_assert(MISC_OFF + 64 <= BYTES, "shared memory layout");
     // TMEM columns: D of tile t at 32 t; A part p of tile t at 64 + 16 (2 p + t)
     static constexpr uint32_t A_COL = 64;
@@ -187,6 +189,7 @@ __global__ void __launch_bounds__(256, 2)
     extern __shared__ __align__(1024) uint8_t smem[];
     float2 *ex = reinterpret_cast<float2 *>(smem);
     uint8_t *sW = smem + L::W_OFF;
+    float2 *stw = reinterpret_cast<float2 *>(smem + L::TW_OFF);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L::MISC_OFF);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L::MISC_OFF + 8);
     int *abort_flag = reinterpret_cast<int *>(smem + L::MISC_OFF + 12);
@@ -204,6 +207,10 @@ __global__ void __launch_bounds__(256, 2)
         for (int q = 0; q < PARTS; ++q)
             *reinterpret_cast<uint16_t *>(sW + q * L::W_PLANE + off) = p[q];
     }
+    // the stage twiddles, read every stage by every thread, kept on chip
+    constexpr int TW_N = LOGN == 12 ? 4096 + 256 : 256;
+    for (int e = tid; e < TW_N; e += 256)
+        stw[e] = tw[e];
     if (warp == 0)
         tmem_alloc(tslot, L::COLS);
     if (tid == 0) {
@@ -227,14 +234,14 @@ __global__ void __launch_bounds__(256, 2)
             const float2 *src = in + g * 4096 + tid;   // row u = tid, points x[u + 256 m]
 #pragma unroll
             for (int m = 0; m < 16; ++m)
-                x[m] = src[256 * m];
+                x[m] = __ldcs(src + 256 * m);
         } else {
             const int rho = tid >> 4, j0 = tid & 15;   // row j0 + 16 rho, points x_rho[j0 + 16 m]
             const bool valid = g * 16 + rho < rows;
             const float2 *src = in + (g * 16 + rho) * 256 + j0;
 #pragma unroll
             for (int m = 0; m < 16; ++m)
-                x[m] = valid ? src[16 * m] : make_float2(0.f, 0.f);
+                x[m] = valid ? __ldcs(src + 16 * m) : make_float2(0.f, 0.f);
         }
     };
 
@@ -335,13 +342,13 @@ __global__ void __launch_bounds__(256, 2)
                     if (s == 0) {   // row u = j0 + 16 j1 -> row j0 + 16 k0, point j1
 #pragma unroll
                         for (int k = 1; k < 16; ++k)
-                            y[k] = cmul(y[k], __ldg(&tw[k * 256 + tid]));
+                            y[k] = cmul(y[k], stw[k * 256 + tid]);
                         rbase = tid & 15;
                         mp = tid >> 4;
                     } else {        // row j0 + 16 k0 -> row k0 + 16 k1, point j0
 #pragma unroll
                         for (int k = 1; k < 16; ++k)
-                            y[k] = cmul(y[k], __ldg(&tw[4096 + k * 16 + (tid & 15)]));
+                            y[k] = cmul(y[k], stw[4096 + k * 16 + (tid & 15)]);
                         rbase = tid >> 4;
                         mp = tid & 15;
                     }
@@ -349,7 +356,7 @@ __global__ void __launch_bounds__(256, 2)
                 } else {            // row j0 + 16 rho -> row k0 + 16 rho, point j0
 #pragma unroll
                     for (int k = 1; k < 16; ++k)
-                        y[k] = cmul(y[k], __ldg(&tw[k * 16 + (tid & 15)]));
+                        y[k] = cmul(y[k], stw[k * 16 + (tid & 15)]);
                     rbase = 16 * (tid >> 4);
                     rstep = 1;
                     mp = tid & 15;
@@ -367,7 +374,7 @@ __global__ void __launch_bounds__(256, 2)
                 float2 *dst = out + g * 4096 + tid;
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
-                    dst[256 * k] = make_float2(y[k].x, y[k].y * cout);
+                    __stcs(dst + 256 * k, make_float2(y[k].x, y[k].y * cout));
             } else {
                 // row k0 + 16 rho = tid: X_rho[k0 + 16 k1]
                 const int rho = tid >> 4, k0 = tid & 15;
@@ -375,7 +382,7 @@ __global__ void __launch_bounds__(256, 2)
                     float2 *dst = out + (g * 16 + rho) * 256 + k0;
 #pragma unroll
                     for (int k = 0; k < 16; ++k)
-                        dst[16 * k] = make_float2(y[k].x, y[k].y * cout);
+                        __stcs(dst + 16 * k, make_float2(y[k].x, y[k].y * cout));
                 }
             }
         }
