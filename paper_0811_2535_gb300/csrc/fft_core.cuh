@@ -178,6 +178,8 @@ struct Layout {
     {
         if constexpr (LAY >= 0)
             return (pw << LAY) + f;
+        else if constexpr (LAY == -2)
+            return f * (N + N / 16 + 1) + pw;   // odd pitch: row-wise and column-wise lanes both conflict-free
         else
             return f * (N + N / 16) + pw;
     }

@@ -1,12 +1,19 @@
 // Internal interfaces between the plan (moa_fft.cu), the pass kernels
 // (pass_kernels.cu) and the twiddle generator (twiddle.cu).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace moa {
 
-enum PassKind { PASS_ROW = 0, PASS_COL = 1, PASS_TC = 2 };
+enum PassKind {
+    PASS_ROW = 0,
+    PASS_COL = 1,
+    PASS_TC = 2,
+    PASS_LIFT3 = 3   // fused second and third pass of a three-level lift (lift3.cu);
+                     // logF = log2 cA, logN = log2 cB
+};
 
 enum PassFlags {
     FLAG_CONJ_IN = 1,    // conjugate on load (sign +1 via conj(F_-(conj x)))
@@ -50,6 +57,10 @@ cudaError_t launch_pass(const PassDesc &d, const float2 *in, float2 *out, const 
 // usable when the driver exposes cuTensorMapEncodeTiled.  The input must be
 // 16-byte aligned.
 bool pipe_supported();
+// Tiled TMA tensor map of 8-byte elements (complex64 moved as 64-bit words):
+// dims / box in elements, innermost first; strides in bytes of dims 1..rank-1.
+bool encode_c64_map(CUtensorMap *map, const void *base, int rank, const uint64_t *dims, const uint64_t *strides,
+                    const uint32_t *box);
 cudaError_t prepare_pipe_kernels();
 cudaError_t launch_pipe_pass(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
                              cudaStream_t stream, int *status);
@@ -65,6 +76,33 @@ cudaError_t launch_tc_pass(const PassDesc &d, bool bf16, const float2 *in, float
 // wait for the products gives up.
 cudaError_t launch_umma_pass(const PassDesc &d, bool bf16, const float2 *in, float2 *out, const float2 *tw, int flags,
                              cudaStream_t stream, int *status);
+// Fused second and third pass of a three-level lifted 1-D transform of
+// n = r * cA * cB points (lift3.cu).  The queue is implicit (the middle
+// tiles of unit u, then `lag` units later the last tiles of unit u);
+// `ticket` is followed by two counters per unit (middle tiles finished, last
+// tiles that have read the unit); `ring` holds `ring_units` units of the
+// intermediate, unit u in slot u % ring_units.
+struct Lift3Launch {
+    // TMA tensor maps in device global memory: the workspace as
+    // [B r cA rows][cB] (box 4096/cA x cA) and the ring as
+    // [ring rows][cA][cB] (box cB x 1 x 4096/cB)
+    const CUtensorMap *map_mid, *map_last;
+    int lag;
+    int *ticket;
+    float2 *ring;
+    int ring_units;
+    int nunits;
+    int grid;
+    const float2 *lo, *hi;   // two-level table of w_c^e, c = cA * cB
+    int h;
+    int loga, logb, logr;
+    int middle_per_unit;     // middle-pass tiles per unit (= cA)
+    int ex_entries;          // exchange buffer entries (complex64) in shared memory
+    size_t smem_bytes;       // dynamic shared memory per block
+};
+int lift3_blocks_per_sm();
+cudaError_t launch_lift3(const Lift3Launch &l, float2 *out, const float2 *stage_a, const float2 *stage_b, int flags,
+                         cudaStream_t stream, int *status);
 cudaError_t generate_full_stage(float2 *dst, int64_t M, int64_t M1, cudaStream_t stream);
 // Shared memory bytes and threads per block of a pass.
 size_t pass_smem_bytes(const PassDesc &d);

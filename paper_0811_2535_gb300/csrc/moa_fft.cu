@@ -53,6 +53,9 @@ struct moa_fft_plan_s {
     int opt_lr = -1;              // log2 r of a lifted 1-D transform
     int opt_pipe = -1;            // 0: generic kernels only, 1: pipelined strided kernels allowed
     int opt_batch_dlr = 0;        // batched: log2 r offset from floor(log2 n / 2)
+    int opt_lift3 = -1;           // 1-D: 1 = three-level lift (r = 256, fused second/third pass)
+    moa::Lift3Launch l3{};
+    void *l3_block = nullptr;     // two-level table of w_c, task queue, ticket and unit counters
     // batched plans (moa_fft_plan_batched): one persistent launch
     bool batched = false;
     moa::BatchLaunch bl{};
@@ -180,6 +183,9 @@ cudaError_t dev_alloc(void **p, size_t bytes)
 
 void free_plan_memory(moa_fft_plan_s *p)
 {
+    if (p->l3_block)
+        cudaFree(p->l3_block);
+    p->l3_block = nullptr;
     if (p->batch_block)
         cudaFree(p->batch_block);
     p->batch_block = nullptr;
@@ -216,6 +222,28 @@ moa_status_t build_passes(moa_fft_plan_s *p)
             p->passes.push_back(row_pass(L, B, 1, BUF_IN, BUF_OUT));
             return MOA_OK;
         }
+        // three-level lift: r = 256 columns pass, then the c = n / 256 point
+        // rows as cA x cB in one fused launch (lift3.cu)
+        const bool lift3 =
+            L >= 21 && L <= 24 && (p->opt_lift3 >= 0 ? p->opt_lift3 == 1 : env_int("MOA_LIFT3", 0) == 1);
+        if (lift3) {
+            const int lc = L - 8;
+            p->split_r = 256;
+            p->split_c = int64_t(1) << lc;
+            p->passes.push_back(col_pass(8, B, p->split_c, 1, BUF_IN, BUF_WS));
+            PassDesc d{};
+            d.kind = moa::PASS_LIFT3;
+            d.logF = (lc + 1) / 2;   // cA
+            d.logN = lc / 2;         // cB
+            d.O = B * 256;
+            d.C = 1;
+            d.Rt = 1;
+            d.src = BUF_WS;
+            d.dst = BUF_OUT;
+            p->passes.push_back(d);
+            p->workspace_bytes = (size_t)p->total * sizeof(float2);
+            return MOA_OK;
+        }
         int lr = p->opt_lr >= 0 ? p->opt_lr : env_int("MOA_SPLIT_LOG2R", L / 2);
         if (lr < 1 || lr > 12 || L - lr < 1 || L - lr > 12)
             lr = L / 2;
@@ -242,12 +270,93 @@ moa_status_t build_passes(moa_fft_plan_s *p)
     return MOA_OK;
 }
 
+// Device block of the fused second/third pass of a three-level lift: the
+// two-level table of w_c (c = cA cB), the ticket and two counters per unit
+// (the queue itself is decoded from the ticket), then a ring of four units
+// of the intermediate (it stays in L2: rewriting a slot does not send the
+// previous unit to DRAM).
+moa_status_t build_lift3(moa_fft_plan_s *p, const PassDesc &d)
+{
+    const int la = d.logF, lb = d.logN, lc = la + lb;
+    const int h = (lc + 1) / 2;
+    const int64_t rows = d.O;                           // B * r rows of c points
+    const int64_t per_unit_rows = int64_t(1) << (12 - lb);
+    const int64_t units = rows / per_unit_rows;
+    const int per_unit = 1 << la;                       // middle tiles per unit = last tiles per unit
+    if (units >= (int64_t(1) << 18) || rows % per_unit_rows)
+        return MOA_ERR_UNSUPPORTED;
+    const int lag = (int)std::min<int64_t>(2, units);
+    const int64_t ntasks = 2 * units * per_unit;
+    if (ntasks >= (int64_t(1) << 30))
+        return MOA_ERR_UNSUPPORTED;
+    const size_t lo_b = ((size_t(1) << h) * sizeof(float2) + 255) & ~size_t(255);
+    const size_t hi_b = ((size_t(1) << (lc - h)) * sizeof(float2) + 255) & ~size_t(255);
+    const int ring_units = (int)std::min<int64_t>(4, units);
+    const size_t ring_b = (size_t)ring_units * (size_t)per_unit_rows * ((size_t)1 << lc) * sizeof(float2);
+    const size_t t_b = (((size_t)(1 + 2 * units) * sizeof(int)) + 255) & ~size_t(255);
+    const size_t m_b = 2 * sizeof(CUtensorMap);   // the two tensor maps (128-byte aligned at this offset)
+    void *blk = nullptr;
+    if (dev_alloc(&blk, lo_b + hi_b + t_b + m_b + ring_b) != cudaSuccess)
+        return MOA_ERR_ALLOC;
+    p->l3_block = blk;
+    char *base = static_cast<char *>(blk);
+    float2 *lo = reinterpret_cast<float2 *>(base);
+    float2 *hi = reinterpret_cast<float2 *>(base + lo_b);
+    if (moa::generate_two_level(lo, hi, lc, h, 0) != cudaSuccess)
+        return MOA_ERR_CUDA;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return MOA_ERR_CUDA;
+    moa::Lift3Launch &l = p->l3;
+    l.lag = lag;
+    l.ticket = reinterpret_cast<int *>(base + lo_b + hi_b);
+    CUtensorMap *maps = reinterpret_cast<CUtensorMap *>(base + lo_b + hi_b + t_b);
+    l.ring = reinterpret_cast<float2 *>(base + lo_b + hi_b + t_b + m_b);
+    l.ring_units = ring_units;
+    l.nunits = (int)units;
+    l.grid = (int)std::min<int64_t>((int64_t)sms * moa::lift3_blocks_per_sm(), ntasks);
+    l.lo = lo;
+    l.hi = hi;
+    l.h = h;
+    l.loga = la;
+    l.logb = lb;
+    l.logr = 8;
+    l.middle_per_unit = per_unit;
+    const int fa = 1 << (12 - la), fb = 1 << (12 - lb);
+    const int ca = 1 << la, cb = 1 << lb;
+    // shared memory: landing buffer (4096 points), exchange buffer, twiddle table
+    l.ex_entries = (std::max((ca + ca / 16) * fa, fb * (cb + cb / 16 + 1)) + 15) & ~15;
+    l.smem_bytes = (size_t)(4096 + l.ex_entries + 16 * fa) * sizeof(float2) + 64;
+    // TMA views: the workspace as [B r cA rows][cB] (middle tiles: cA rows x
+    // 4096/cA columns), the ring as [ring rows][cA][cB] (last tiles: the
+    // unit's 4096/cB rows at one k2)
+    const uint64_t dm[2] = {(uint64_t)cb, (uint64_t)(rows << la)};
+    const uint64_t sm_[1] = {(uint64_t)cb * sizeof(float2)};
+    const uint32_t bm[2] = {(uint32_t)fa, (uint32_t)ca};
+    const uint64_t dl[3] = {(uint64_t)cb, (uint64_t)ca, (uint64_t)(ring_units * per_unit_rows)};
+    const uint64_t sl[2] = {(uint64_t)cb * sizeof(float2), ((uint64_t)1 << lc) * sizeof(float2)};
+    const uint32_t bl[3] = {(uint32_t)cb, 1, (uint32_t)fb};
+    CUtensorMap host_maps[2];
+    if (!moa::encode_c64_map(&host_maps[0], p->workspace, 2, dm, sm_, bm) ||
+        !moa::encode_c64_map(&host_maps[1], l.ring, 3, dl, sl, bl))
+        return MOA_ERR_UNSUPPORTED;
+    if (cudaMemcpy(maps, host_maps, sizeof(host_maps), cudaMemcpyHostToDevice) != cudaSuccess)
+        return MOA_ERR_CUDA;
+    l.map_mid = maps;
+    l.map_last = maps + 1;
+    return MOA_OK;
+}
+
 moa_status_t allocate_and_fill(moa_fft_plan_s *p)
 {
     // layout of the device block: status word, stage tables, two-level tables
     bool need_stage[13] = {false};
-    for (const PassDesc &d : p->passes)
+    for (const PassDesc &d : p->passes) {
         need_stage[d.logN] = true;
+        if (d.kind == moa::PASS_LIFT3)
+            need_stage[d.logF] = true;
+    }
     size_t offs[13] = {0};
     size_t bytes = 256;  // status word
     for (int l = 1; l <= 12; ++l) {
@@ -340,6 +449,12 @@ moa_status_t allocate_and_fill(moa_fft_plan_s *p)
         p->tw.hi = hi;
         p->tw.h = h;
     }
+    for (const PassDesc &d : p->passes)
+        if (d.kind == moa::PASS_LIFT3) {
+            const moa_status_t st = build_lift3(p, d);
+            if (st != MOA_OK)
+                return st;
+        }
     if (cudaDeviceSynchronize() != cudaSuccess)
         return MOA_ERR_CUDA;
     return MOA_OK;
@@ -565,6 +680,11 @@ moa_status_t run_pass(moa_fft_plan_s *p, size_t i, const void *in, void *out, cu
         if (i + 1 == np)
             flags |= moa::FLAG_CONJ_OUT;
     }
+    if (d.kind == moa::PASS_LIFT3)   // reads the workspace through the tensor map made at plan time
+        return moa::launch_lift3(p->l3, buf(d.dst), p->tw.stage[d.logF], p->tw.stage[d.logN], flags, s,
+                                 p->d_status) == cudaSuccess
+                   ? MOA_OK
+                   : MOA_ERR_CUDA;
     if (d.kind == moa::PASS_TC) {
         const bool bf16 = p->dtype == MOA_C64_TC_BF16;
         const cudaError_t e = d.umma ? moa::launch_umma_pass(d, bf16, buf(d.src), buf(d.dst), p->tw.tc, flags, s,
@@ -736,7 +856,7 @@ moa_status_t run(moa_fft_plan_s *p, const void *in, void *out, void *stream, int
 
 // Build a plan (not yet registered) with optional fixed choices.
 moa_status_t make_plan(moa_fft_plan_s **out, const int64_t *n, int dims, int64_t batch, int sign, int dtype,
-                       int64_t total, int opt_lr, int opt_pipe)
+                       int64_t total, int opt_lr, int opt_pipe, int opt_lift3 = -1)
 {
     *out = nullptr;
     moa_fft_plan_s *p = new (std::nothrow) moa_fft_plan_s();
@@ -751,6 +871,7 @@ moa_status_t make_plan(moa_fft_plan_s **out, const int64_t *n, int dims, int64_t
     p->total = total;
     p->opt_lr = opt_lr;
     p->opt_pipe = opt_pipe;
+    p->opt_lift3 = opt_lift3;
     moa_status_t st = build_passes(p);
     if (st == MOA_OK)
         st = allocate_and_fill(p);
@@ -810,12 +931,12 @@ moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int6
     if (dtype != MOA_C64 && !(dims == 1 && (n[0] == 256 || n[0] == 4096)))
         return MOA_ERR_UNSUPPORTED;
 
-    int opt_lr = -1, opt_pipe = -1;
+    int opt_lr = -1, opt_pipe = -1, opt_lift3 = -1;
     const int L = ilog2(n[0]);
-    if (dims == 1 && L > 12 && autotune_enabled() && !env_set("MOA_SPLIT_LOG2R")) {
-        const std::string key = device_tag() + ":1d2:" + std::to_string(L) + ":" + std::to_string(batch);
+    if (dims == 1 && L > 12 && autotune_enabled() && !env_set("MOA_SPLIT_LOG2R") && !env_set("MOA_LIFT3")) {
+        const std::string key = device_tag() + ":1d3:" + std::to_string(L) + ":" + std::to_string(batch);
         std::string v;
-        if (tune_get(key, v) && sscanf(v.c_str(), "%d %d", &opt_lr, &opt_pipe) == 2) {
+        if (tune_get(key, v) && sscanf(v.c_str(), "%d %d %d", &opt_lr, &opt_pipe, &opt_lift3) == 3) {
             // cached choice
         } else {
             float best = INFINITY;
@@ -823,7 +944,8 @@ moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int6
             for (int lr = std::max(1, L - 12); lr <= std::min(12, L - 1); ++lr) {
                 for (int pipe = 2; pipe >= (try_generic ? 0 : 2); --pipe) {
                     moa_fft_plan_s *cand = nullptr;
-                    const moa_status_t st = make_plan(&cand, n, dims, batch, sign, dtype, total, lr, try_generic ? pipe : -1);
+                    const moa_status_t st =
+                        make_plan(&cand, n, dims, batch, sign, dtype, total, lr, try_generic ? pipe : -1, 0);
                     if (st != MOA_OK)
                         return st;
                     const bool used_blk = std::any_of(cand->passes.begin(), cand->passes.end(),
@@ -842,17 +964,37 @@ moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int6
                         best = ms;
                         opt_lr = lr;
                         opt_pipe = try_generic ? pipe : -1;
+                        opt_lift3 = 0;
                     }
                     if (!used_pipe)
                         break;   // no pass of this split has a pipelined form
                 }
             }
+            // the three-level lift (r = 256, fused second and third pass)
+            if (L >= 21 && L <= 24) {
+                moa_fft_plan_s *cand = nullptr;
+                const moa_status_t st = make_plan(&cand, n, dims, batch, sign, dtype, total, -1, -1, 1);
+                if (st == MOA_OK) {
+                    const float ms = time_exec(cand);
+                    free_plan_memory(cand);
+                    delete cand;
+                    if (ms < best) {
+                        best = ms;
+                        opt_lr = -1;
+                        opt_pipe = -1;
+                        opt_lift3 = 1;
+                    }
+                } else if (st != MOA_ERR_UNSUPPORTED) {
+                    return st;
+                }
+            }
             if (std::isfinite(best))
-                tune_put(key, std::to_string(opt_lr) + " " + std::to_string(opt_pipe));
+                tune_put(key, std::to_string(opt_lr) + " " + std::to_string(opt_pipe) + " " +
+                                  std::to_string(opt_lift3));
         }
     }
     moa_fft_plan_s *p = nullptr;
-    const moa_status_t st = make_plan(&p, n, dims, batch, sign, dtype, total, opt_lr, opt_pipe);
+    const moa_status_t st = make_plan(&p, n, dims, batch, sign, dtype, total, opt_lr, opt_pipe, opt_lift3);
     if (st != MOA_OK)
         return st;
     {
@@ -1029,6 +1171,8 @@ moa_status_t moa_fft_pass_info(moa_fft_plan_t plan, int index, char *name, size_
     else if (d.kind == moa::PASS_TC)
         snprintf(buf, sizeof(buf), d.umma ? "tc_umma_kernel<%d,%d>" : "tc_row_kernel<%d,%d>",
                  plan->dtype == MOA_C64_TC_BF16 ? 1 : 0, d.logN);
+    else if (d.kind == moa::PASS_LIFT3)
+        snprintf(buf, sizeof(buf), "lift3_kernel<%d,%d>", d.logF, d.logN);
     else if (d.pipe && (d.kind == moa::PASS_COL || d.blk == 2))
         snprintf(buf, sizeof(buf), "pipe_col_kernel<%d,%d,%d>", d.logN, d.tw4, d.blk);
     else if (d.pipe)

@@ -489,6 +489,26 @@ cudaError_t set_pipe_attrs()
 
 bool pipe_supported() { return encode_fn() != nullptr; }
 
+bool encode_c64_map(CUtensorMap *map, const void *base, int rank, const uint64_t *dims, const uint64_t *strides,
+                    const uint32_t *box)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc || rank < 1 || rank > 5)
+        return false;
+    cuuint64_t d[5], st[4];
+    cuuint32_t b[5], es[5];
+    for (int i = 0; i < rank; ++i) {
+        d[i] = dims[i];
+        b[i] = box[i];
+        es[i] = 1;
+        if (i + 1 < rank)
+            st[i] = strides[i];
+    }
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, (cuuint32_t)rank, const_cast<void *>(base), d, st, b, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t prepare_pipe_kernels()
 {
     int dev = 0;

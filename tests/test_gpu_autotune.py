@@ -39,9 +39,10 @@ def test_autotuned_split_is_cached_and_correct(env, tmp_path, monkeypatch):
     t_first = time.perf_counter() - t0
     info = plan.info()
     text = cache.read_text()
-    line = [ln for ln in text.splitlines() if ":1d:19:3 " in ln]
+    line = [ln for ln in text.splitlines() if ":1d3:19:3 " in ln]
     assert len(line) == 1, text
-    lr, pipe = (int(v) for v in line[0].split()[1:3])
+    lr, pipe, lift3 = (int(v) for v in line[0].split()[1:4])
+    assert lift3 == 0          # the three-level lift is a candidate from 2^21 on
     assert info["split_r"] == 1 << lr and 7 <= lr <= 12
     x = inputs.uniform((3, n), 77)
     y = plan.exec(torch.from_numpy(x).cuda()).cpu().numpy()

@@ -229,3 +229,28 @@ def test_blocked_workspace_lifted(env, L, lr, batch, sign, monkeypatch):
     plan.destroy()
     ref = oracle_ref(env, x, [n], batch, sign)
     assert per_transform_rel(y, ref, batch).max() <= TOL
+
+
+@pytest.mark.parametrize("L,batch", [(24, 1), (23, 2), (22, 1), (21, 3)])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_three_level_lift(env, L, batch, sign, monkeypatch):
+    """n = 256 x cA x cB: the r = 256 column pass, then the second and third
+    pass fused in one work-queue launch (middle tiles in place, last tiles
+    waiting on per-unit counters), against the oracle."""
+    torch, moafft, _ = env
+    from paper_0811_2535_gb300 import inputs
+    monkeypatch.setenv("MOA_LIFT3", "1")
+    n = 1 << L
+    x = inputs.uniform((batch, n), 6200 + L)
+    plan = moafft.Plan([n], batch, sign)
+    la, lb = (L - 7) // 2, (L - 8) // 2
+    names = [plan.pass_info(i)["kernel"] for i in range(plan.info()["passes"])]
+    assert names == ["col_pass_kernel<8,1>", "lift3_kernel<%d,%d>" % (la, lb)], names
+    xd = torch.from_numpy(x).cuda()
+    y = plan.exec(xd).cpu().numpy()
+    y2 = plan.exec(xd).cpu().numpy()          # the queue and counters are reset per exec
+    assert plan.status() == 0
+    plan.destroy()
+    ref = oracle_ref(env, x, [n], batch, sign)
+    assert per_transform_rel(y, ref, batch).max() <= TOL
+    assert np.array_equal(y, y2)
