@@ -39,6 +39,13 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
+// Programmatic dependent launch: let the next kernel in the stream start
+// launching now, and wait (before touching data the previous kernel wrote)
+// until that previous kernel has completed.  Both are no-ops for kernels
+// launched without the programmatic-serialization attribute.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait_prior() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
@@ -169,8 +176,12 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     float2 *E = reinterpret_cast<float2 *>(smem_raw);
     float2 *H = E + PipeSmem::E_entries<LOGN>();
-    float2 *tk = H + PipeSmem::H_entries<LOGN>();    // [16][4] four-step twiddle factors
-    uint64_t *bar = reinterpret_cast<uint64_t *>(tk + 64);   // [0]: H, [1]: second half in E
+    // four-step twiddle w_n^(col*(tau + T*k)) = A * B_k, both looked up before
+    // the tile's data arrives: tk = [2][16][4] B_k per column, As = [2][threads] A,
+    // double-buffered by tile parity
+    float2 *tk = H + PipeSmem::H_entries<LOGN>();
+    float2 *As = tk + 128;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(As + 2 * (N / 4));   // [0]: H, [1]: second half in E
     int *abort_flag = reinterpret_cast<int *>(bar + 2);
 
     const int tid = threadIdx.x;
@@ -191,6 +202,7 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
         }
     };
 
+    pdl_launch_dependents();
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -200,6 +212,7 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
     __syncthreads();
     int tile = blockIdx.x;
     if (tid == 0 && tile < ntiles) {
+        pdl_wait_prior();   // the input may be the previous kernel's output
         issue_half(tile, 0, H, &bar[0]);
         issue_half(tile, 1, E, &bar[1]);
     }
@@ -208,6 +221,13 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
         const int o = tile >> logTpo;
         const int col = ((tile & tpo_mask) << 2) + f;
         const int next = tile + (int)gridDim.x;
+        float2 *tkb = tk + 64 * parity, *Ab = As + (N / 4) * parity;
+        if constexpr (TW4) {
+            // look the twiddles up while the tile is still landing
+            if (tau < 16)
+                tkb[tau * 4 + f] = two_level_tw(tw_lo, tw_hi, tw_h, (int64_t)col * (T * tau));
+            Ab[tid] = two_level_tw(tw_lo, tw_hi, tw_h, (int64_t)col * tau);
+        }
         if (tid == 0) {
             bounded_wait(&bar[0], parity, status, abort_flag);
             bounded_wait(&bar[1], parity, status, abort_flag);
@@ -236,11 +256,6 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
             for (int r = 0; r < 16; ++r)
                 v[r].y = -v[r].y;
         }
-        if constexpr (TW4) {
-            if (tau < 16)
-                tk[tau * 4 + f] = two_level_tw(tw_lo, tw_hi, tw_h, (int64_t)col * (T * tau));
-        }
-
         three_stages<LOGN>(v, E, tau, f, tw, [&] {
             if (tid == 0 && next < ntiles) {
                 fence_proxy_async();
@@ -249,10 +264,10 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
         });
 
         if constexpr (TW4) {
-            const float2 A = two_level_tw(tw_lo, tw_hi, tw_h, (int64_t)col * tau);
+            const float2 A = Ab[tid];
 #pragma unroll
             for (int k = 0; k < 16; ++k)
-                v[k] = cmul(v[k], cmul(A, tk[k * 4 + f]));
+                v[k] = cmul(v[k], cmul(A, tkb[k * 4 + f]));
         }
         if (flags & FLAG_CONJ_OUT) {
 #pragma unroll
@@ -304,6 +319,7 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
             bulk_load(dst + r * PITCH, in + (o0 + r) * N + h * NH, NH * (uint32_t)sizeof(float2), b);
     };
 
+    pdl_launch_dependents();
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -313,6 +329,7 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
     __syncthreads();
     int tile = blockIdx.x;
     if (tid == 0 && tile < ntiles) {
+        pdl_wait_prior();   // the input may be the previous kernel's output
         issue_half(tile, 0, H, &bar[0]);
         issue_half(tile, 1, E, &bar[1]);
     }
@@ -401,7 +418,31 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-template <int LOGN> size_t col_smem() { return PipeSmem::bytes<LOGN>(); }
+// E, H, the twiddle tables tk [2][64] and As [2][N/4], two mbarriers and a flag
+template <int LOGN> size_t col_smem()
+{
+    return (size_t)(PipeSmem::E_entries<LOGN>() + PipeSmem::H_entries<LOGN>() + 128 + 2 * ((1 << LOGN) / 4)) * 8 + 64;
+}
+// Launch `kern`; with `dependent`, as a programmatic dependent launch (the
+// kernel starts while the previous kernel in the stream finishes and waits
+// for it with griddepcontrol.wait before reading its output).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_maybe_dependent(void (*kern)(KArgs...), int grid, int threads, size_t smem, cudaStream_t stream,
+                                   int dependent, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = dependent ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 template <int LOGN> size_t rowT_smem() { return PipeSmem::bytes<LOGN>(); }
 
 int g_num_sms = 0;
@@ -443,21 +484,12 @@ cudaError_t launch_col(const PassDesc &d, int64_t O, int64_t C, int blk, const f
     const int ntiles = (int)(O << logTpo);
     const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
     const size_t smem = col_smem<LOGN>();
-    const dim3 g(grid), b(1 << (LOGN - 2));
     const int Ci = (int)C;
-    if (blk == 2)
-        pipe_col_kernel<LOGN, false, 2><<<g, b, smem, stream>>>(map, out, Ci, logTpo, ntiles, tw.stage[LOGN], tw.lo,
-                                                                tw.hi, tw.h, flags, status);
-    else if (d.tw4 && blk == 1)
-        pipe_col_kernel<LOGN, true, 1><<<g, b, smem, stream>>>(map, out, Ci, logTpo, ntiles, tw.stage[LOGN], tw.lo,
-                                                               tw.hi, tw.h, flags, status);
-    else if (d.tw4)
-        pipe_col_kernel<LOGN, true, 0><<<g, b, smem, stream>>>(map, out, Ci, logTpo, ntiles, tw.stage[LOGN], tw.lo,
-                                                               tw.hi, tw.h, flags, status);
-    else
-        pipe_col_kernel<LOGN, false, 0><<<g, b, smem, stream>>>(map, out, Ci, logTpo, ntiles, tw.stage[LOGN], tw.lo,
-                                                                tw.hi, tw.h, flags, status);
-    return cudaGetLastError();
+    auto kern = blk == 2 ? pipe_col_kernel<LOGN, false, 2>
+                         : (d.tw4 && blk == 1 ? pipe_col_kernel<LOGN, true, 1>
+                                              : (d.tw4 ? pipe_col_kernel<LOGN, true, 0> : pipe_col_kernel<LOGN, false, 0>));
+    return launch_maybe_dependent(kern, grid, 1 << (LOGN - 2), smem, stream, flags & FLAG_PDL, map, out, Ci, logTpo,
+                                  ntiles, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags, status);
 }
 
 template <int LOGN>
@@ -466,9 +498,8 @@ cudaError_t launch_rowT(const PassDesc &d, const float2 *in, float2 *out, const 
 {
     const int ntiles = (int)((d.O + 3) / 4);
     const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
-    pipe_rowT_kernel<LOGN><<<grid, 1 << (LOGN - 2), rowT_smem<LOGN>(), stream>>>(in, out, d.O, d.Rt, ntiles,
-                                                                                  tw.stage[LOGN], flags, status);
-    return cudaGetLastError();
+    return launch_maybe_dependent(pipe_rowT_kernel<LOGN>, grid, 1 << (LOGN - 2), rowT_smem<LOGN>(), stream,
+                                  flags & FLAG_PDL, in, out, d.O, d.Rt, ntiles, tw.stage[LOGN], flags, status);
 }
 
 template <int LOGN>
