@@ -114,6 +114,16 @@ struct PipeSmem {
     {
         return (size_t)(E_entries<LOGN>() + H_entries<LOGN>() + 64) * 8 + 64;
     }
+    // column kernel: rows of the next tile that land early (while the tile
+    // computes) in a buffer of their own; the rest lands in the exchange
+    // buffer after its last use.  As many whole 256-row boxes as fit next to
+    // the exchange buffer, at most all but one.
+    template <int LOGN> __host__ __device__ static constexpr int early_rows()
+    {
+        return ((((232448 - E_entries<LOGN>() * 8 - 1280) / 32) / 256) * 256) < (1 << LOGN) - 256
+                   ? (((232448 - E_entries<LOGN>() * 8 - 1280) / 32) / 256) * 256
+                   : (1 << LOGN) - 256;
+    }
 };
 
 // Bounded wait on an mbarrier phase by one thread; on timeout the status word
@@ -172,33 +182,31 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
                     int tw_h, int flags, int *status)
 {
     using Sc = Sched<LOGN>;
-    constexpr int N = Sc::N, T = Sc::T, NH = N / 2;
+    constexpr int N = Sc::N, T = Sc::T;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     float2 *E = reinterpret_cast<float2 *>(smem_raw);
     float2 *H = E + PipeSmem::E_entries<LOGN>();
-    // four-step twiddle w_n^(col*(tau + T*k)) = A * B_k, both looked up before
-    // the tile's data arrives: tk = [2][16][4] B_k per column, As = [2][threads] A,
-    // double-buffered by tile parity
-    float2 *tk = H + PipeSmem::H_entries<LOGN>();
-    float2 *As = tk + 128;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(As + 2 * (N / 4));   // [0]: H, [1]: second half in E
+    constexpr int HR = PipeSmem::early_rows<LOGN>();   // rows landing in H; rows HR..N-1 land in E
+    float2 *tk = H + 4 * HR;                           // [16][4] four-step twiddle factors
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tk + 64);   // [0]: H, [1]: the rest in E
     int *abort_flag = reinterpret_cast<int *>(bar + 2);
 
     const int tid = threadIdx.x;
     const int f = tid & 3, tau = tid >> 2;
     const unsigned tpo_mask = (1u << logTpo) - 1;
 
-    // rows [h*N/2, (h+1)*N/2) of the tile's four columns, as boxes of 256 rows x 32 bytes
+    // rows [0, HR) (h = 0) or [HR, N) (h = 1) of the tile's four columns, as
+    // boxes of 256 rows x 32 bytes
     auto issue_half = [&](int tile, int h, float2 *dst, uint64_t *b) {
         const int o = tile >> logTpo;
         const int c0 = (tile & tpo_mask) << 2;
-        mbar_arrive_expect_tx(b, NH * 4 * (uint32_t)sizeof(float2));
-#pragma unroll
-        for (int k = 0; k < NH / 256; ++k) {
+        const int r0 = h ? HR : 0, nb = (h ? N - HR : HR) / 256;
+        mbar_arrive_expect_tx(b, nb * 256 * 4 * (uint32_t)sizeof(float2));
+        for (int k = 0; k < nb; ++k) {
             if constexpr (BLK == 2)
-                tma_load_3d(dst + k * 256 * 4, &tmap, b, 0, c0 >> 2, (o * N + h * NH + k * 256) >> 2);
+                tma_load_3d(dst + k * 256 * 4, &tmap, b, 0, c0 >> 2, (o * N + r0 + k * 256) >> 2);
             else
-                tma_load_2d(dst + k * 256 * 4, &tmap, b, 2 * c0, o * N + h * NH + k * 256);
+                tma_load_2d(dst + k * 256 * 4, &tmap, b, 2 * c0, o * N + r0 + k * 256);
         }
     };
 
@@ -221,13 +229,6 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
         const int o = tile >> logTpo;
         const int col = ((tile & tpo_mask) << 2) + f;
         const int next = tile + (int)gridDim.x;
-        float2 *tkb = tk + 64 * parity, *Ab = As + (N / 4) * parity;
-        if constexpr (TW4) {
-            // look the twiddles up while the tile is still landing
-            if (tau < 16)
-                tkb[tau * 4 + f] = two_level_tw(tw_lo, tw_hi, tw_h, (int64_t)col * (T * tau));
-            Ab[tid] = two_level_tw(tw_lo, tw_hi, tw_h, (int64_t)col * tau);
-        }
         if (tid == 0) {
             bounded_wait(&bar[0], parity, status, abort_flag);
             bounded_wait(&bar[1], parity, status, abort_flag);
@@ -238,13 +239,14 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
         parity ^= 1u;
 
         // element tau + T*q lands in register (q % NB0)*R0 + q / NB0 (stage-0 order);
-        // q < 8 is in the first half (H), q >= 8 in the second (E)
+        // rows below HR (q < HR / T) are in H, the others in E
         constexpr int R0 = 1 << Sc::rlog(0), NB0 = 16 / R0;
+        static_assert(HR % T == 0, "early rows must be whole row blocks");
         float2 v[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-            const float2 *src = q < 8 ? H : E;
-            v[(q % NB0) * R0 + q / NB0] = src[(tau + T * (q & 7)) * 4 + f];
+            const float2 *src = q * T < HR ? H + (tau + T * q) * 4 : E + (tau + T * q - HR) * 4;
+            v[(q % NB0) * R0 + q / NB0] = src[f];
         }
         __syncthreads();   // H and E have been read
         if (tid == 0 && next < ntiles) {
@@ -256,6 +258,11 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
             for (int r = 0; r < 16; ++r)
                 v[r].y = -v[r].y;
         }
+        if constexpr (TW4) {
+            if (tau < 16)
+                tk[tau * 4 + f] = two_level_tw(tw_lo, tw_hi, tw_h, (int64_t)col * (T * tau));
+        }
+
         three_stages<LOGN>(v, E, tau, f, tw, [&] {
             if (tid == 0 && next < ntiles) {
                 fence_proxy_async();
@@ -264,10 +271,10 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
         });
 
         if constexpr (TW4) {
-            const float2 A = Ab[tid];
+            const float2 A = two_level_tw(tw_lo, tw_hi, tw_h, (int64_t)col * tau);
 #pragma unroll
             for (int k = 0; k < 16; ++k)
-                v[k] = cmul(v[k], cmul(A, tkb[k * 4 + f]));
+                v[k] = cmul(v[k], cmul(A, tk[k * 4 + f]));
         }
         if (flags & FLAG_CONJ_OUT) {
 #pragma unroll
@@ -418,10 +425,11 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-// E, H, the twiddle tables tk [2][64] and As [2][N/4], two mbarriers and a flag
+// E, H (the early rows of the next tile), the twiddle table tk [16][4], two
+// mbarriers and a flag
 template <int LOGN> size_t col_smem()
 {
-    return (size_t)(PipeSmem::E_entries<LOGN>() + PipeSmem::H_entries<LOGN>() + 128 + 2 * ((1 << LOGN) / 4)) * 8 + 64;
+    return (size_t)(PipeSmem::E_entries<LOGN>() + 4 * PipeSmem::early_rows<LOGN>() + 64) * 8 + 64;
 }
 // Launch `kern`; with `dependent`, as a programmatic dependent launch (the
 // kernel starts while the previous kernel in the stream finishes and waits
