@@ -114,31 +114,54 @@ __device__ __forceinline__ void large_col_tile(const float2 *x, float2 *b, int c
 }
 
 // One row tile of a large transform: c = 2^LOGC points per row, 4096/c
-// rows starting at row 4096/c * tile, transposed store into X (r rows).
+// rows starting at row 4096/c * tile, transposed store into X (r rows).  The
+// rows are read with c/16 consecutive threads per row (whole runs of one row
+// per warp) and stage 0 runs in that order; the first exchange (row-major,
+// odd row pitch: conflict-free for both orders) hands the data to the
+// row-interleaved order in which the other stages run and the transposed
+// stores cover whole segments of consecutive rows.
 template <int LOGC>
 __device__ __forceinline__ void large_row_tile(const float2 *b, float2 *X, int r, int tile, const BatchTables &tb,
                                             float2 *sm, int flags)
 {
     using Sc = Sched<LOGC>;
     constexpr int N = Sc::N, T = Sc::T;
-    constexpr int LOGF = 12 - LOGC;   // 4096/c rows per tile, adjacent lanes
+    constexpr int LOGT = LOGC - 4;
+    constexpr int LOGF = 12 - LOGC;   // 4096/c rows per tile
     constexpr int F = 1 << LOGF;
     const int tid = threadIdx.x;
-    const int f = tid & (F - 1), tau = tid >> LOGF;
     constexpr int R0 = 1 << Sc::rlog(0), NB0 = Sc::P / R0;
-    const int k1 = tile * F + f;
+    const int fb = tid & (F - 1), tau_b = tid >> LOGF;
+    constexpr int LR = F >= 16 ? -2 : (F == 8 ? -3 : -4);   // row pitch padding for F rows
     float2 v[16];
-    const float2 *src = b + (int64_t)k1 * N + tau;
+    if constexpr (Sc::S == 1) {
+        // one stage: one thread per row, no exchange
+        const float2 *src = b + (int64_t)(tile * F + fb) * N;
 #pragma unroll
-    for (int q = 0; q < Sc::P; ++q)
-        v[(q % NB0) * R0 + q / NB0] = src[q * T];
-    fft_tile<LOGC, LOGF>(v, sm, tau, f, tb.stage[LOGC]);
+        for (int q = 0; q < Sc::P; ++q)
+            v[q] = src[q];
+        stage_compute<LOGC, 0>(v, 0, tb.stage[LOGC]);
+    } else {
+        const int tau_a = tid & (T - 1), fa = tid >> LOGT;
+        const float2 *src = b + (int64_t)(tile * F + fa) * N + tau_a;
+#pragma unroll
+        for (int q = 0; q < Sc::P; ++q)
+            v[(q % NB0) * R0 + q / NB0] = src[q * T];
+        stage_compute<LOGC, 0>(v, tau_a, tb.stage[LOGC]);
+        stage_write<LOGC, 0, LR>(v, sm, tau_a, fa);
+        __syncthreads();
+        stage_read<LOGC, 1, LR>(v, sm, tau_b, fb);
+        __syncthreads();
+        stage_compute<LOGC, 1>(v, tau_b, tb.stage[LOGC]);
+        run_stages<LOGC, 2, LR>(v, sm, tau_b, fb, tb.stage[LOGC]);
+    }
     if (flags & FLAG_CONJ_OUT) {
 #pragma unroll
         for (int k = 0; k < Sc::P; ++k)
             v[k].y = -v[k].y;
     }
-    float2 *dst = X + k1 + (int64_t)tau * r;
+    const int k1 = tile * F + fb;
+    float2 *dst = X + k1 + (int64_t)tau_b * r;
 #pragma unroll
     for (int k = 0; k < Sc::P; ++k)
         dst[(int64_t)k * T * r] = v[k];
@@ -236,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
                    int *status)
 {
     const BatchTables &tb = *tbp;
-    __shared__ float2 sm[4352];   // exchange buffer: 4096 points + padding
+    __shared__ float2 sm[4480];   // exchange buffer: 4096 points + padding (up to 128 rows of N + N/16 + 1)
     __shared__ int s_task, s_flag;
     int *counters = ticket + 1;
     for (;;) {

@@ -178,8 +178,10 @@ struct Layout {
     {
         if constexpr (LAY >= 0)
             return (pw << LAY) + f;
-        else if constexpr (LAY == -2)
-            return f * (N + N / 16 + 1) + pw;   // odd pitch: row-wise and column-wise lanes both conflict-free
+        else if constexpr (LAY <= -2)
+            // row pitch N + N/16 + 2^(-2-LAY): with 16, 8 or 4 rows per half-warp
+            // (LAY = -2, -3, -4) both row-wise and row-interleaved lanes are conflict-free
+            return f * (N + N / 16 + (1 << (-2 - LAY))) + pw;
         else
             return f * (N + N / 16) + pw;
     }
