@@ -321,6 +321,85 @@ def tensor_core_report(torch, moafft, inputs, dev, iters, with_oracle):
     return rep
 
 
+def autograd_report(torch, moafft, inputs, dev, iters):
+    """Differentiation workload: batch 256 x n = 2^18 (seed 4), loss =
+    sum |H * F(x)|^2 with a fixed complex filter H, backward through the
+    adjoint kernel (MoaFFTFunction).  Reports the whole forward + backward
+    step and the two transforms alone (exec + exec_adjoint), each moving
+    32n bytes per transform through HBM (two passes)."""
+    n, batch = 1 << 18, 256
+    H, x_h = inputs.spectral_filter(n, batch, inputs.SEED_GRADIENT)
+    Hd = torch.from_numpy(H).to(dev)
+    x = torch.from_numpy(x_h.reshape(batch, n)).to(dev).requires_grad_(True)
+    plan = moafft.Plan([n], batch, -1)
+    stream = torch.cuda.current_stream(dev)
+
+    def fwd_bwd():
+        x.grad = None
+        y = moafft.fft_autograd(x, plan)
+        loss = (Hd * y).abs().pow(2).sum()
+        loss.backward()
+
+    y0 = torch.empty_like(x.detach())
+    g0 = torch.empty_like(y0)
+
+    def transforms():
+        plan.exec(x.detach(), y0, stream=stream)
+        plan.exec_adjoint(y0, g0, stream=stream)
+
+    out = {"workload": "256 x 1-D 2^18 (seed 4), loss sum|H*F(x)|^2, backward by the adjoint kernel",
+           "passes": [plan.pass_info(i)["kernel"] for i in range(plan.info()["passes"])]}
+    for name, fn in (("fwd_bwd_step", fwd_bwd), ("fft_plus_adjoint", transforms)):
+        for _ in range(3):
+            fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(iters):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) / iters * 1e3
+        out[name + "_us"] = us
+    t = out["fft_plus_adjoint_us"]
+    out["fft_GFLOPs"] = 2 * batch * flops((n,)) / t / 1e3
+    out["fft_algorithmic_GBps"] = 2 * 32.0 * n * batch / t / 1e3
+    if plan.status() != 0:
+        raise RuntimeError("device status word set in the autograd report")
+    plan.destroy()
+    return out
+
+
+def small_report(torch, moafft, inputs, dev, iters):
+    """n = 2^10, batch 1 (seed 0): one exec (a single 4096-point-tile
+    launch) and the forward + inverse round trip, as latencies."""
+    n = 1 << 10
+    x = torch.from_numpy(inputs.uniform((n,), inputs.SEED_SMALL)).to(dev)
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+    plan = moafft.Plan([n], 1, -1)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": "1-D 2^10, batch 1 (seed 0)", "kernel": plan.pass_info(0)["kernel"]}
+    for name, fn in (("exec", lambda: plan.exec(x, y, stream=stream)),
+                     ("round_trip", lambda: (plan.exec(x, y, stream=stream), plan.exec_adjoint(y, z, stream=stream)))):
+        for _ in range(10):
+            fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(iters):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name + "_us"] = e0.elapsed_time(e1) / iters * 1e3
+    zz = z.cpu().numpy() / n
+    out["round_trip_rel_err"] = float(abs(zz - x.cpu().numpy()).max() / abs(x.cpu().numpy()).max())
+    plan.destroy()
+    return out
+
+
 def run_moa(args):
     import numpy as np
     import torch
@@ -485,6 +564,8 @@ def run_moa(args):
         if p.status() != 0:
             raise RuntimeError("device status word set after the benchmark")
     batched = None if args.no_batched else batched_report(torch, moafft, inputs, dev, max(3, min(args.steps, 20)))
+    autograd = None if args.no_batched else autograd_report(torch, moafft, inputs, dev, max(3, min(args.steps, 20)))
+    small = None if args.no_batched else small_report(torch, moafft, inputs, dev, 200)
     tensor_core = None if args.no_batched else tensor_core_report(torch, moafft, inputs, dev, max(3, min(args.steps, 20)),
                                                                   not args.no_oracle)
 
@@ -496,7 +577,7 @@ def run_moa(args):
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "passes_per_step": launches_per_step},
                 "roofline": roofline, "lifted_1d": lifted, "batched_uneven": batched,
-                "tensor_core": tensor_core, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
+                "tensor_core": tensor_core, "autograd": autograd, "small_1d": small, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches_per_step * args.steps, "rel_l2": parity or None,
                 "parity_ok": (all(v <= TOL for v in parity.values()) if parity else None), "kernels": kernels}
         print(json.dumps(line), flush=True)
@@ -512,7 +593,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["moa", "reference"], default="moa")
     ap.add_argument("--no-oracle", action="store_true", help="skip the CPU oracle parity/baseline leg")
-    ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch and tensor-core comparisons")
+    ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch, tensor-core, autograd and small-n reports")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
