@@ -19,8 +19,8 @@ enum PassFlags {
     FLAG_CONJ_IN = 1,    // conjugate on load (sign +1 via conj(F_-(conj x)))
     FLAG_CONJ_OUT = 2,   // conjugate on store
     FLAG_TW4 = 4,        // multiply column outputs by w_{N*C}^(k*i) (four-step twiddle)
-    FLAG_PDL = 8         // the pass follows another of the same exec: pipelined kernels may use a
-                         // programmatic dependent launch (they wait for the previous kernel on the device)
+    FLAG_PDL = 8         // launch as a programmatic dependent launch of the previous kernel in the
+                         // stream (the row, column and pipelined pass kernels wait for it on the device)
 };
 
 // One kernel launch: N-point transforms (N = 2^logN <= 4096) along one axis.

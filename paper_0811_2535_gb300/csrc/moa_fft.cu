@@ -680,7 +680,10 @@ moa_status_t run_pass(moa_fft_plan_s *p, size_t i, const void *in, void *out, cu
         if (i + 1 == np)
             flags |= moa::FLAG_CONJ_OUT;
     }
-    if (i > 0 && env_int("MOA_PDL", 1))
+    // every pass (the first one too) may start while the kernel before it in
+    // the stream finishes: the pass kernels wait on the device before they
+    // touch its buffers (MOA_PDL=0: plain stream order)
+    if (env_int("MOA_PDL", 1))
         flags |= moa::FLAG_PDL;
     if (d.kind == moa::PASS_LIFT3)   // reads the workspace through the tensor map made at plan time
         return moa::launch_lift3(p->l3, buf(d.dst), p->tw.stage[d.logF], p->tw.stage[d.logN], flags, s,

@@ -12,6 +12,7 @@
 
 #include "fft_core.cuh"
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace moa {
 
@@ -42,6 +43,8 @@ __global__ void __launch_bounds__(1024) col_pass_kernel(const float2 *in, float2
     const int64_t base = (int64_t)o * ((int64_t)Sc::N * C) + col + (int64_t)tau * C;
     const int step = Sc::T * C;
 
+    pdl_launch_dependents();
+    pdl_wait_prior();   // `in` may be the previous kernel's output, `out` its input
     float2 v[16];
     {
         constexpr int R0 = 1 << Sc::rlog(0);
@@ -107,6 +110,8 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(const float2 *in, float2
     const int tau = TRANS ? (tid >> logF) : (tid & (Sc::T - 1));
     const int64_t o = ((int64_t)blockIdx.x << logF) + f;
     const bool active = o < O;
+    pdl_launch_dependents();
+    pdl_wait_prior();   // `in` may be the previous kernel's output, `out` its input
     float2 v[16];
     if (active) {
         constexpr int R0 = 1 << Sc::rlog(0);
@@ -154,22 +159,14 @@ cudaError_t launch_typed(const PassDesc &d, const float2 *in, float2 *out, const
         while ((int64_t(1) << logTpo) < (d.C >> d.logF))
             ++logTpo;
         const int64_t grid = d.O << logTpo;
-        if (d.tw4)
-            col_pass_kernel<LOGN, true><<<(unsigned)grid, threads, smem, stream>>>(
-                in, out, (int)d.C, d.logF, logTpo, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags);
-        else
-            col_pass_kernel<LOGN, false><<<(unsigned)grid, threads, smem, stream>>>(
-                in, out, (int)d.C, d.logF, logTpo, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags);
-    } else {
-        const int64_t grid = (d.O + (int64_t(1) << d.logF) - 1) >> d.logF;
-        if (d.Rt > 1)
-            row_pass_kernel<LOGN, true><<<(unsigned)grid, threads, smem, stream>>>(in, out, d.O, d.Rt, d.logF,
-                                                                               tw.stage[LOGN], flags);
-        else
-            row_pass_kernel<LOGN, false><<<(unsigned)grid, threads, smem, stream>>>(in, out, d.O, d.Rt, d.logF,
-                                                                                tw.stage[LOGN], flags);
+        return launch_maybe_dependent(d.tw4 ? col_pass_kernel<LOGN, true> : col_pass_kernel<LOGN, false>,
+                                      (unsigned)grid, threads, smem, stream, flags & FLAG_PDL, in, out, (int)d.C,
+                                      d.logF, logTpo, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags);
     }
-    return cudaGetLastError();
+    const int64_t grid = (d.O + (int64_t(1) << d.logF) - 1) >> d.logF;
+    return launch_maybe_dependent(d.Rt > 1 ? row_pass_kernel<LOGN, true> : row_pass_kernel<LOGN, false>,
+                                  (unsigned)grid, threads, smem, stream, flags & FLAG_PDL, in, out, d.O, d.Rt,
+                                  d.logF, tw.stage[LOGN], flags);
 }
 
 template <int LOGN>

@@ -25,6 +25,7 @@
 
 #include "fft_core.cuh"
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace moa {
 
@@ -38,13 +39,6 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 }
 
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-// Programmatic dependent launch: let the next kernel in the stream start
-// launching now, and wait (before touching data the previous kernel wrote)
-// until that previous kernel has completed.  Both are no-ops for kernels
-// launched without the programmatic-serialization attribute.
-__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait_prior() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
@@ -431,26 +425,6 @@ template <int LOGN> size_t col_smem()
 {
     return (size_t)(PipeSmem::E_entries<LOGN>() + 4 * PipeSmem::early_rows<LOGN>() + 64) * 8 + 64;
 }
-// Launch `kern`; with `dependent`, as a programmatic dependent launch (the
-// kernel starts while the previous kernel in the stream finishes and waits
-// for it with griddepcontrol.wait before reading its output).
-template <typename... KArgs, typename... Args>
-cudaError_t launch_maybe_dependent(void (*kern)(KArgs...), int grid, int threads, size_t smem, cudaStream_t stream,
-                                   int dependent, Args... args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = dependent ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
-}
-
 template <int LOGN> size_t rowT_smem() { return PipeSmem::bytes<LOGN>(); }
 
 int g_num_sms = 0;

@@ -254,3 +254,48 @@ def test_three_level_lift(env, L, batch, sign, monkeypatch):
     ref = oracle_ref(env, x, [n], batch, sign)
     assert per_transform_rel(y, ref, batch).max() <= TOL
     assert np.array_equal(y, y2)
+
+
+def test_pdl_chain_across_plans(env, monkeypatch):
+    """Every pass is a programmatic dependent launch of the kernel before it
+    in the stream and waits for it on the device.  A chain of execs of
+    different plans on one stream, each reading the buffer the previous one
+    wrote and writing the buffer it read, gives the same bits as the same
+    chain in plain stream order with a synchronize after every exec."""
+    torch, moafft, _ = env
+    from paper_0811_2535_gb300 import inputs
+    n = 1 << 24
+    x = torch.from_numpy(inputs.uniform((n,), 6400)).cuda()
+    monkeypatch.setenv("MOA_AUTOTUNE", "0")
+    specs = [([n], 1, -1, moafft.MOA_C64, {}), ([4096, 4096], 1, 1, moafft.MOA_C64, {}),
+             ([256, 256, 256], 1, -1, moafft.MOA_C64, {}), ([1 << 20], 16, 1, moafft.MOA_C64, {}),
+             ([4096], 4096, -1, moafft.MOA_C64_TC_FP16, {}), ([4096], 4096, 1, moafft.MOA_C64, {}),
+             ([n], 1, -1, moafft.MOA_C64, {"MOA_LIFT3": "1"}), ([1 << 12, 1 << 12], 1, 1, moafft.MOA_C64, {})]
+    plans = []
+    for shape, batch, sign, dtype, envs in specs:
+        for k, v in envs.items():
+            monkeypatch.setenv(k, v)
+        plans.append(moafft.Plan(shape, batch, sign, dtype))
+        for k in envs:
+            monkeypatch.delenv(k)
+
+    def chain(pdl):
+        monkeypatch.setenv("MOA_PDL", "1" if pdl else "0")
+        a, b = x.clone(), torch.empty_like(x)
+        for p in plans:
+            p.exec(a, out=b)
+            if not pdl:
+                torch.cuda.synchronize()
+            a, b = b, a
+        torch.cuda.synchronize()
+        return a.cpu().numpy()
+
+    ref = chain(False)
+    got = chain(True)
+    again = chain(True)
+    for p in plans:
+        assert p.status() == 0
+        p.destroy()
+    assert np.isfinite(ref).all()
+    assert np.array_equal(got, ref)
+    assert np.array_equal(again, ref)
