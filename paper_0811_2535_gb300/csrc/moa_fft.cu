@@ -680,10 +680,12 @@ moa_status_t run_pass(moa_fft_plan_s *p, size_t i, const void *in, void *out, cu
         if (i + 1 == np)
             flags |= moa::FLAG_CONJ_OUT;
     }
-    // every pass (the first one too) may start while the kernel before it in
-    // the stream finishes: the pass kernels wait on the device before they
-    // touch its buffers (MOA_PDL=0: plain stream order)
-    if (env_int("MOA_PDL", 1))
+    // programmatic dependent launch (MOA_PDL=0: plain stream order): every
+    // pass after the first, and a first pass that is a pipelined kernel (it
+    // lands its first tile as soon as the kernel before it completes).  A
+    // generic first pass launches in plain order: measured on the GB300, it
+    // ran slower when its blocks were placed early behind a pipelined kernel.
+    if (env_int("MOA_PDL", 1) && (i > 0 || d.pipe))
         flags |= moa::FLAG_PDL;
     if (d.kind == moa::PASS_LIFT3)   // reads the workspace through the tensor map made at plan time
         return moa::launch_lift3(p->l3, buf(d.dst), p->tw.stage[d.logF], p->tw.stage[d.logN], flags, s,

@@ -43,7 +43,6 @@ __global__ void __launch_bounds__(1024) col_pass_kernel(const float2 *in, float2
     const int64_t base = (int64_t)o * ((int64_t)Sc::N * C) + col + (int64_t)tau * C;
     const int step = Sc::T * C;
 
-    pdl_launch_dependents();
     pdl_wait_prior();   // `in` may be the previous kernel's output, `out` its input
     float2 v[16];
     {
@@ -91,6 +90,7 @@ __global__ void __launch_bounds__(1024) col_pass_kernel(const float2 *in, float2
 #pragma unroll
     for (int k = 0; k < Sc::P; ++k)
         dst[k * step] = v[k];
+    pdl_launch_dependents();   // after the stores: the next kernel launches as the last blocks finish
 }
 
 template <int LOGN, bool TRANS>
@@ -110,7 +110,6 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(const float2 *in, float2
     const int tau = TRANS ? (tid >> logF) : (tid & (Sc::T - 1));
     const int64_t o = ((int64_t)blockIdx.x << logF) + f;
     const bool active = o < O;
-    pdl_launch_dependents();
     pdl_wait_prior();   // `in` may be the previous kernel's output, `out` its input
     float2 v[16];
     if (active) {
@@ -146,6 +145,7 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(const float2 *in, float2
         for (int k = 0; k < Sc::P; ++k)
             dst[k * step] = v[k];
     }
+    pdl_launch_dependents();
 }
 
 template <int LOGN>

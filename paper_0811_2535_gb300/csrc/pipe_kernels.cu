@@ -204,7 +204,6 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
         }
     };
 
-    pdl_launch_dependents();
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -223,6 +222,8 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
         const int o = tile >> logTpo;
         const int col = ((tile & tpo_mask) << 2) + f;
         const int next = tile + (int)gridDim.x;
+        if (next >= ntiles)
+            pdl_launch_dependents();   // the block's last tile: let the next kernel launch
         if (tid == 0) {
             bounded_wait(&bar[0], parity, status, abort_flag);
             bounded_wait(&bar[1], parity, status, abort_flag);
@@ -320,7 +321,6 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
             bulk_load(dst + r * PITCH, in + (o0 + r) * N + h * NH, NH * (uint32_t)sizeof(float2), b);
     };
 
-    pdl_launch_dependents();
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -339,6 +339,8 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
         const int64_t o = (int64_t)tile * 4 + f;
         const bool active = o < O;
         const int next = tile + (int)gridDim.x;
+        if (next >= ntiles)
+            pdl_launch_dependents();   // the block's last tile: let the next kernel launch
         if (tid == 0) {
             bounded_wait(&bar[0], parity, status, abort_flag);
             bounded_wait(&bar[1], parity, status, abort_flag);
