@@ -155,7 +155,7 @@ def kernel_src_hash(kernel: str) -> str:
     d = os.path.join(ROOT, "paper_0811_2535_gb300", "csrc")
     own = "pipe_kernels.cu" if kernel.startswith("pipe_") else "pass_kernels.cu"
     h = hashlib.sha256()
-    for name in (own, "fft_core.cuh", "internal.h"):
+    for name in (own, "fft_core.cuh", "internal.h", "pdl.cuh"):
         with open(os.path.join(d, name), "rb") as fh:
             h.update(name.encode())
             h.update(fh.read())
