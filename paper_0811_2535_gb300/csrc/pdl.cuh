@@ -1,14 +1,19 @@
 // Programmatic dependent launch between consecutive kernels of a stream.
 //
 // A kernel launched with the programmatic-serialization attribute may start
-// while the kernel before it in the stream is still running: its blocks take
-// the SMs that the earlier kernel's last blocks leave free, set up shared
-// memory and then wait (griddepcontrol.wait) until the earlier kernel has
-// completed and its writes are visible.  Every pass kernel that is launched
-// this way waits before its first access to global memory other than the
-// plan's own twiddle tables, so reads after writes and writes after reads of
-// the previous kernel's buffers stay ordered as in plain stream order.  Both
-// instructions are no-ops for a kernel launched without the attribute.
+// once every block of the kernel before it in the stream has signalled
+// (griddepcontrol.launch_dependents) or exited: its blocks take the SMs that
+// the earlier kernel's last blocks leave free, set up shared memory and then
+// wait (griddepcontrol.wait) until the earlier kernel has completed and its
+// writes are visible.  Every pass kernel that is launched this way waits
+// before it touches global memory other than the plan's own twiddle tables
+// (a generic pass kernel: every thread at its start; a pipelined one: the
+// thread that issues the first TMA load, before a block barrier that all
+// other global accesses follow), so reads after writes and writes after reads
+// of the previous kernel's buffers stay ordered as in plain stream order.
+// The pass kernels signal late (after their stores, or when a persistent
+// block starts its last tile).  Both instructions are no-ops for a kernel
+// launched without the attribute.
 #pragma once
 #include <cuda_runtime.h>
 
