@@ -20,6 +20,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -150,15 +151,23 @@ def whole_job_gflops(flops_per_step: float, steps: int, world: int, max_ms: floa
     return world * flops_per_step * steps / (max_ms * 1e-3) / 1e9
 
 
+def _code_only(src: str) -> str:
+    """C/CUDA source without comments and blank lines (edits to comments do
+    not change the kernels a capture was taken on)."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    lines = (re.sub(r"//.*", "", ln).rstrip() for ln in src.splitlines())
+    return "\n".join(ln for ln in lines if ln.strip())
+
+
 def kernel_src_hash(kernel: str) -> str:
-    """Hash of the source files a kernel is built from (its family)."""
+    """Hash of the code of the source files a kernel is built from (its family)."""
     d = os.path.join(ROOT, "paper_0811_2535_gb300", "csrc")
     own = "pipe_kernels.cu" if kernel.startswith("pipe_") else "pass_kernels.cu"
     h = hashlib.sha256()
     for name in (own, "fft_core.cuh", "internal.h", "pdl.cuh"):
-        with open(os.path.join(d, name), "rb") as fh:
+        with open(os.path.join(d, name), encoding="utf-8") as fh:
             h.update(name.encode())
-            h.update(fh.read())
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
