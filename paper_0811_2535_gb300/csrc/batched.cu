@@ -187,9 +187,6 @@ __device__ __forceinline__ void run_small(const BatchTask &t, const int64_t *off
     }
 }
 
-// Upper bound on polls of a completion counter (with a short sleep each);
-// far beyond the few microseconds a column tile takes.
-constexpr int kMaxPolls = 1 << 22;
 
 __device__ __forceinline__ int load_acquire(const int *p)
 {
@@ -199,7 +196,8 @@ __device__ __forceinline__ int load_acquire(const int *p)
 }
 
 __device__ __forceinline__ void run_large(const BatchTask &t, const int64_t *offs, const float2 *in, float2 *out, float2 *ws,
-                          int *counters, const BatchTables &tb, float2 *sm, int flags, int *status, int *s_flag)
+                          int *counters, const BatchTables &tb, float2 *sm, int flags, int *status, int *s_flag,
+                          int max_polls, int wait_extra)
 {
     const int64_t base = offs[t.first];
     const int c = 1 << (t.logn - t.logr), r = 1 << t.logr;
@@ -225,10 +223,10 @@ __device__ __forceinline__ void run_large(const BatchTask &t, const int64_t *off
     }
     // row tile: wait until every column tile of this transform is done
     if (threadIdx.x == 0) {
-        const int need = 1 << (t.logn - 12);
+        const int need = (1 << (t.logn - 12)) + wait_extra;
         int polls = 0, ok = 1;
         while (load_acquire(&counters[t.first]) < need) {
-            if (++polls >= kMaxPolls) {
+            if (++polls >= max_polls) {
                 atomicExch(status, 6);   // MOA_ERR_TIMEOUT
                 ok = 0;
                 break;
@@ -256,7 +254,7 @@ __device__ __forceinline__ void run_large(const BatchTask &t, const int64_t *off
 __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
     batched_kernel(const BatchTask *__restrict__ tasks, int ntasks, int *ticket, const int64_t *__restrict__ offs,
                    const float2 *in, float2 *out, float2 *ws, const BatchTables *__restrict__ tbp, int flags,
-                   int *status)
+                   int *status, int max_polls, int wait_extra)
 {
     const BatchTables &tb = *tbp;
     __shared__ float2 sm[4480];   // exchange buffer: 4096 points + padding (up to 128 rows of N + N/16 + 1)
@@ -274,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
         if (t.kind == 0)
             run_small(t, offs, in, out, tb, sm, flags);
         else
-            run_large(t, offs, in, out, ws, counters, tb, sm, flags, status, &s_flag);
+            run_large(t, offs, in, out, ws, counters, tb, sm, flags, status, &s_flag, max_polls, wait_extra);
         __syncthreads();   // the exchange buffer is reused by the next task
     }
 }
@@ -291,7 +289,7 @@ cudaError_t launch_batched(const BatchLaunch &b, const float2 *in, float2 *out, 
     if (e != cudaSuccess)
         return e;
     batched_kernel<<<b.grid, kThreads, 0, stream>>>(b.tasks, b.ntasks, b.ticket, b.offs, in, out, b.ws, b.tables,
-                                                    flags, status);
+                                                    flags, status, b.max_polls, b.wait_extra);
     return cudaGetLastError();
 }
 

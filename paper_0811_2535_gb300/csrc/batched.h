@@ -42,6 +42,13 @@ struct BatchLaunch {
     float2 *ws;                // workspace mirroring the input layout (large tasks)
     const BatchTables *tables;   // device copy of the table pointers
     unsigned grid;
+    // Bounded waits of the row tiles: at most max_polls polls of the counter.
+    // Fault injection for tests (MOA_FAULT_WAIT=1 at plan time): wait_extra = 1
+    // makes every row tile wait for one column tile more than its transform
+    // has, a count nothing reaches, so each wait runs out and reports
+    // MOA_ERR_TIMEOUT (the tile is skipped; nothing hangs or faults).
+    int max_polls;
+    int wait_extra;
 };
 
 int batched_blocks_per_sm();

@@ -652,6 +652,12 @@ moa_status_t build_batched(moa_fft_plan_s *p, const int64_t *lengths, int64_t co
     p->bl.tables = reinterpret_cast<const moa::BatchTables *>(base + tables_off);
     const int64_t grid = std::min<int64_t>(resident, (int64_t)queue.size());
     p->bl.grid = (unsigned)std::max<int64_t>(grid, 1);
+    // a row tile polls its counter (64 ns sleep each) far beyond the few
+    // microseconds a column tile takes; MOA_FAULT_WAIT=1 (tests) makes every
+    // row-tile wait unreachable and short, so the timeout path runs
+    const bool fault_wait = env_int("MOA_FAULT_WAIT", 0) == 1;
+    p->bl.max_polls = fault_wait ? 256 : (1 << 22);
+    p->bl.wait_extra = fault_wait ? 1 : 0;
     if (cudaDeviceSynchronize() != cudaSuccess)
         return MOA_ERR_CUDA;
     return MOA_OK;

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libmoafft.so")
 MOA_C64, MOA_C64_TC_FP16, MOA_C64_TC_BF16 = 0, 1, 2
 STATUS = {0: "MOA_OK", 1: "MOA_ERR_INVALID_ARG", 2: "MOA_ERR_INVALID_SIZE", 3: "MOA_ERR_UNSUPPORTED",
           4: "MOA_ERR_ALLOC", 5: "MOA_ERR_CUDA", 6: "MOA_ERR_TIMEOUT"}
+MOA_OK, MOA_ERR_TIMEOUT = 0, 6
 
 # every symbol the header declares, with (restype, argtypes)
 _P = ctypes.c_void_p

@@ -100,3 +100,32 @@ def test_uneven_workload_full(env):
     lengths, vecs = inputs.uneven_batch(4096, inputs.SEED_UNEVEN)
     lengths = [int(n) for n in lengths]
     check(env, lengths, vecs, run_batched(env, lengths, vecs, -1), -1)
+
+
+def test_wait_timeout_is_reported_and_contained(env, monkeypatch):
+    """Failure detection without a GPU fault: with MOA_FAULT_WAIT=1 at plan
+    time every row tile of a large transform waits for a column-tile count
+    that nothing reaches, with a short poll limit.  The launch completes, the
+    status word reads MOA_ERR_TIMEOUT, the transforms that need no wait (the
+    small ones) are still right, and the next plan on the same context runs
+    correctly."""
+    torch, moafft, _ = env
+    from paper_0811_2535_gb300 import inputs
+    lengths = [1 << 13, 64, 1 << 16, 256, 1 << 14, 4096, 128]
+    vecs = [inputs.uniform(n, 1300 + i) for i, n in enumerate(lengths)]
+    x = torch.from_numpy(np.concatenate(vecs)).cuda()
+    monkeypatch.setenv("MOA_FAULT_WAIT", "1")
+    plan = moafft.BatchedPlan(lengths, -1)
+    monkeypatch.delenv("MOA_FAULT_WAIT")
+    out = torch.zeros_like(x)
+    plan.exec(x, out)
+    torch.cuda.synchronize()
+    assert plan.status() == moafft.MOA_ERR_TIMEOUT
+    assert plan.status() == 0          # reading the status clears it
+    offs = plan.offsets()
+    plan.destroy()
+    y = out.cpu().numpy()
+    small = [i for i, n in enumerate(lengths) if n <= 4096]
+    check(env, [lengths[i] for i in small], [vecs[i] for i in small],
+          [y[offs[i]:offs[i] + lengths[i]] for i in small], -1)
+    check(env, lengths, vecs, run_batched(env, lengths, vecs, -1), -1)
