@@ -425,7 +425,11 @@ def run_moa(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+        if local != 0:
+            dist.barrier()   # local rank 0 builds (or finds built) the library first
     _build.build()
+    if world > 1 and local == 0:
+        torch.distributed.barrier()
     moafft.lib()
 
     plans, xs, outs, pass_kernels, pass_bytes = [], [], [], {}, {}
