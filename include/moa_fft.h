@@ -99,7 +99,12 @@ MOA_API moa_status_t moa_fft_plan_batched(moa_fft_plan_t *plan, const int64_t *l
                                   int sign, int dtype);
 
 /* Run the planned transform (sign as planned) from `in` to `out` on
- * `stream`.  Asynchronous; no allocation; capturable. */
+ * `stream`.  Asynchronous; no allocation; capturable.  Stream order holds:
+ * a pass may be launched as a programmatic dependent launch of the kernel
+ * before it in the stream (the caller's included), so its blocks can become
+ * resident while that kernel finishes, but they wait on the device for it to
+ * complete before reading or writing any buffer (MOA_PDL=0 in the
+ * environment turns this off). */
 MOA_API moa_status_t moa_fft_exec(moa_fft_plan_t plan, const void *in, void *out, void *stream);
 
 /* Run the adjoint of the planned transform: the unnormalised transform of
