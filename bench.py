@@ -496,10 +496,11 @@ def run_moa(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for _ in range(args.steps):
-        step()
-    t1.record(stream)
+    with torch.cuda.nvtx.range("moafft: timed steps"):
+        t0.record(stream)
+        for _ in range(args.steps):
+            step()
+        t1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -509,11 +510,12 @@ def run_moa(args):
     # transforms (an event between two kernels keeps the second from starting
     # early, so these add up to a little more than the timed steps)
     events = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps * len(WORKLOAD) + 1)]
-    events[0].record(stream)
-    ei = 1
-    for _ in range(args.steps):
-        ei = step(events, ei)
-    torch.cuda.synchronize()
+    with torch.cuda.nvtx.range("moafft: per-transform steps"):
+        events[0].record(stream)
+        ei = 1
+        for _ in range(args.steps):
+            ei = step(events, ei)
+        torch.cuda.synchronize()
     per_transform = {}
     k = 0
     for _ in range(args.steps):
@@ -526,20 +528,22 @@ def run_moa(args):
     i1d = [name for name, _ in WORKLOAD].index("1d_2^24")
     b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     nb2b = max(10, args.steps)
-    b0.record(stream)
-    for _ in range(nb2b):
-        plans[i1d].exec(xs[i1d], outs[i1d], stream=stream)
-    b1.record(stream)
+    with torch.cuda.nvtx.range("moafft: 1-D back to back"):
+        b0.record(stream)
+        for _ in range(nb2b):
+            plans[i1d].exec(xs[i1d], outs[i1d], stream=stream)
+        b1.record(stream)
     torch.cuda.synchronize()
     t1d_b2b = b0.elapsed_time(b1) / nb2b
 
     # per-kernel durations: the same number of steps, pass by pass
     pevents = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps * launches_per_step + 1)]
-    pevents[0].record(stream)
-    ei = 1
-    for _ in range(args.steps):
-        ei = pass_step(pevents, ei)
-    torch.cuda.synchronize()
+    with torch.cuda.nvtx.range("moafft: pass-by-pass steps"):
+        pevents[0].record(stream)
+        ei = 1
+        for _ in range(args.steps):
+            ei = pass_step(pevents, ei)
+        torch.cuda.synchronize()
     clocks = sampler.stop()
     per_kernel = {}
     k = 0
@@ -592,8 +596,8 @@ def run_moa(args):
     xstreams = [torch.cuda.Stream(dev) for _ in WORKLOAD]
 
     def e2e_step():
-        for p, a, b, d, xs in zip(plans, hin, hout, dbuf, xstreams):
-            p.exec_host(a, b, d, stream=xs)
+        for p, a, b, d, xst in zip(plans, hin, hout, dbuf, xstreams):
+            p.exec_host(a, b, d, stream=xst)
 
     e2e_step()
     torch.cuda.synchronize()
@@ -601,14 +605,15 @@ def run_moa(args):
         torch.distributed.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for xs in xstreams:
-        xs.wait_event(e0)
-    for _ in range(e2e_steps):
-        e2e_step()
-    for xs in xstreams:
-        stream.wait_stream(xs)
-    e1.record(stream)
+    with torch.cuda.nvtx.range("moafft: end-to-end steps"):
+        e0.record(stream)
+        for xst in xstreams:
+            xst.wait_event(e0)
+        for _ in range(e2e_steps):
+            e2e_step()
+        for xst in xstreams:
+            stream.wait_stream(xst)
+        e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
     io_bytes = sum(8 * numel(s) for _, s in WORKLOAD)

@@ -868,6 +868,53 @@ moa_status_t run(moa_fft_plan_s *p, const void *in, void *out, void *stream, int
 
 
 // Build a plan (not yet registered) with optional fixed choices.
+// Kernel that runs pass d of plan p (the name moa_fft_pass_info reports).
+void pass_name(const moa_fft_plan_s *p, const PassDesc &d, char *buf, size_t len)
+{
+    if (p->batched)
+        snprintf(buf, len, "batched_kernel");
+    else if (d.kind == moa::PASS_TC)
+        snprintf(buf, len, d.umma ? "tc_umma_kernel<%d,%d>" : "tc_row_kernel<%d,%d>",
+                 p->dtype == MOA_C64_TC_BF16 ? 1 : 0, d.logN);
+    else if (d.kind == moa::PASS_LIFT3)
+        snprintf(buf, len, "lift3_kernel<%d,%d>", d.logF, d.logN);
+    else if (d.pipe && (d.kind == moa::PASS_COL || d.blk == 2))
+        snprintf(buf, len, "pipe_col_kernel<%d,%d,%d>", d.logN, d.tw4, d.blk);
+    else if (d.pipe)
+        snprintf(buf, len, "pipe_rowT_kernel<%d>", d.logN);
+    else if (d.kind == moa::PASS_COL)
+        snprintf(buf, len, "col_pass_kernel<%d,%d>", d.logN, d.tw4);
+    else
+        snprintf(buf, len, "row_pass_kernel<%d,%d>", d.logN, d.Rt > 1 ? 1 : 0);
+}
+
+// MOA_LOG=1: plan decisions and autotuner timings on stderr.
+bool log_enabled() { return env_int("MOA_LOG", 0) == 1; }
+
+void log_plan(const moa_fft_plan_s *p, const char *how)
+{
+    if (!log_enabled())
+        return;
+    std::string dims;
+    if (p->batched) {
+        dims = "batched: " + std::to_string(p->bl.ntasks) + " tasks";
+    } else {
+        for (int i = 0; i < p->dims; ++i)
+            dims += (i ? "x" : "") + std::to_string(p->n[i]);
+        dims += " batch " + std::to_string(p->batch);
+    }
+    std::string passes;
+    const size_t np = p->batched ? 1 : p->passes.size();
+    for (size_t i = 0; i < np; ++i) {
+        char buf[64];
+        pass_name(p, p->batched ? PassDesc{} : p->passes[i], buf, sizeof(buf));
+        passes += (i ? " -> " : "") + std::string(buf);
+    }
+    fprintf(stderr, "moafft: plan %s sign %+d dtype %d (%s): split r=%lld c=%lld, workspace %zu bytes, %s\n",
+            dims.c_str(), p->sign, p->dtype, how, (long long)p->split_r, (long long)p->split_c, p->workspace_bytes,
+            passes.c_str());
+}
+
 moa_status_t make_plan(moa_fft_plan_s **out, const int64_t *n, int dims, int64_t batch, int sign, int dtype,
                        int64_t total, int opt_lr, int opt_pipe, int opt_lift3 = -1)
 {
@@ -946,12 +993,14 @@ moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int6
 
     int opt_lr = -1, opt_pipe = -1, opt_lift3 = -1;
     const int L = ilog2(n[0]);
+    const char *how = "defaults or environment overrides";
     if (dims == 1 && L > 12 && autotune_enabled() && !env_set("MOA_SPLIT_LOG2R") && !env_set("MOA_LIFT3")) {
         const std::string key = device_tag() + ":1d3:" + std::to_string(L) + ":" + std::to_string(batch);
         std::string v;
         if (tune_get(key, v) && sscanf(v.c_str(), "%d %d %d", &opt_lr, &opt_pipe, &opt_lift3) == 3) {
-            // cached choice
+            how = "autotuner choice from the cache";
         } else {
+            how = "autotuned";
             float best = INFINITY;
             const bool try_generic = !env_set("MOA_PIPE");
             for (int lr = std::max(1, L - 12); lr <= std::min(12, L - 1); ++lr) {
@@ -969,6 +1018,9 @@ moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int6
                         continue;   // same plan as pipe = 1
                     }
                     const float ms = time_exec(cand);
+                    if (log_enabled())
+                        fprintf(stderr, "moafft: autotune 1-D 2^%d x %lld: log2 r = %d, pipe mode %d: %.1f us\n", L,
+                                (long long)batch, lr, pipe, ms * 1e3f);
                     const bool used_pipe = std::any_of(cand->passes.begin(), cand->passes.end(),
                                                        [](const PassDesc &d) { return d.pipe != 0; });
                     free_plan_memory(cand);
@@ -989,6 +1041,9 @@ moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int6
                 const moa_status_t st = make_plan(&cand, n, dims, batch, sign, dtype, total, -1, -1, 1);
                 if (st == MOA_OK) {
                     const float ms = time_exec(cand);
+                    if (log_enabled())
+                        fprintf(stderr, "moafft: autotune 1-D 2^%d x %lld: three-level lift: %.1f us\n", L,
+                                (long long)batch, ms * 1e3f);
                     free_plan_memory(cand);
                     delete cand;
                     if (ms < best) {
@@ -1010,6 +1065,7 @@ moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int6
     const moa_status_t st = make_plan(&p, n, dims, batch, sign, dtype, total, opt_lr, opt_pipe, opt_lift3);
     if (st != MOA_OK)
         return st;
+    log_plan(p, how);
     {
         std::lock_guard<std::mutex> lk(g_plans_mu);
         g_plans.insert(p);
@@ -1060,6 +1116,9 @@ moa_status_t moa_fft_plan_batched(moa_fft_plan_t *plan, const int64_t *lengths, 
                 if (st != MOA_OK)
                     return st;
                 const float ms = time_exec(cand);
+                if (log_enabled())
+                    fprintf(stderr, "moafft: autotune batched (%lld transforms): log2 r offset %+d: %.1f us\n",
+                            (long long)count, cand_dlr, ms * 1e3f);
                 free_plan_memory(cand);
                 delete cand;
                 if (ms < best) {
@@ -1075,6 +1134,7 @@ moa_status_t moa_fft_plan_batched(moa_fft_plan_t *plan, const int64_t *lengths, 
     const moa_status_t st = make_batched(&p, lengths, count, sign, dtype, dlr);
     if (st != MOA_OK)
         return st;
+    log_plan(p, dlr != 0 ? "log2 r offset from the autotuner" : "default split of the large transforms");
     {
         std::lock_guard<std::mutex> lk(g_plans_mu);
         g_plans.insert(p);
@@ -1179,21 +1239,7 @@ moa_status_t moa_fft_pass_info(moa_fft_plan_t plan, int index, char *name, size_
         return MOA_ERR_INVALID_ARG;
     char buf[64];
     const PassDesc d = plan->batched ? PassDesc{} : plan->passes[index];
-    if (plan->batched)
-        snprintf(buf, sizeof(buf), "batched_kernel");
-    else if (d.kind == moa::PASS_TC)
-        snprintf(buf, sizeof(buf), d.umma ? "tc_umma_kernel<%d,%d>" : "tc_row_kernel<%d,%d>",
-                 plan->dtype == MOA_C64_TC_BF16 ? 1 : 0, d.logN);
-    else if (d.kind == moa::PASS_LIFT3)
-        snprintf(buf, sizeof(buf), "lift3_kernel<%d,%d>", d.logF, d.logN);
-    else if (d.pipe && (d.kind == moa::PASS_COL || d.blk == 2))
-        snprintf(buf, sizeof(buf), "pipe_col_kernel<%d,%d,%d>", d.logN, d.tw4, d.blk);
-    else if (d.pipe)
-        snprintf(buf, sizeof(buf), "pipe_rowT_kernel<%d>", d.logN);
-    else if (d.kind == moa::PASS_COL)
-        snprintf(buf, sizeof(buf), "col_pass_kernel<%d,%d>", d.logN, d.tw4);
-    else
-        snprintf(buf, sizeof(buf), "row_pass_kernel<%d,%d>", d.logN, d.Rt > 1 ? 1 : 0);
+    pass_name(plan, d, buf, sizeof(buf));
     if (name_len > 0) {
         strncpy(name, buf, name_len - 1);
         name[name_len - 1] = '\0';

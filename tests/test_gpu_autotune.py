@@ -75,3 +75,26 @@ def test_autotuned_batched_plan(env, tmp_path, monkeypatch):
         ref = oracle.fft_radix2(v.astype(np.complex128), -1)
         assert np.linalg.norm(y[o:o + n] - ref) / np.linalg.norm(ref) <= TOL
     plan.destroy()
+
+
+def test_plan_log(env, tmp_path):
+    """MOA_LOG=1: the autotuner's timed candidates and the chosen plan are
+    written to stderr (checked in a child process, whose stderr is captured)."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_0811_2535_gb300 import moafft\n"
+            "p = moafft.Plan([1 << 17], 2, -1); p.destroy()\n"
+            "q = moafft.Plan([64, 32], 1, 1); q.destroy()\n") % root
+    envv = dict(os.environ, MOA_LOG="1", MOA_AUTOTUNE="1", MOA_TUNE_CACHE=str(tmp_path / "tune.txt"))
+    for k in ("MOA_SPLIT_LOG2R", "MOA_PIPE", "MOA_BATCH_LOG2R", "MOA_LIFT3"):
+        envv.pop(k, None)
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=envv, timeout=300)
+    assert res.returncode == 0, res.stderr
+    lines = [ln for ln in res.stderr.splitlines() if ln.startswith("moafft: ")]
+    assert any(ln.startswith("moafft: autotune 1-D 2^17 x 2: log2 r = ") for ln in lines), lines
+    plan_lines = [ln for ln in lines if ln.startswith("moafft: plan ")]
+    assert len(plan_lines) == 2, lines
+    assert "131072 batch 2 sign -1" in plan_lines[0] and "autotuned" in plan_lines[0]
+    assert "64x32 batch 1 sign +1" in plan_lines[1] and "row_pass_kernel<5,0> -> col_pass_kernel<6,0>" in plan_lines[1]
