@@ -672,8 +672,14 @@ moa_status_t run_pass(moa_fft_plan_s *p, size_t i, const void *in, void *out, cu
                    ? MOA_OK
                    : MOA_ERR_CUDA;
     }
-    const PassDesc &d = p->passes[i];
+    PassDesc d = p->passes[i];
     const size_t np = p->passes.size();
+    // The blocked intermediate needs pass 1 on the TMA kernel, which needs a
+    // 16-byte aligned input; with an input that is only 8-byte aligned this
+    // exec runs both passes in the natural layout instead (generic column
+    // pass, then the transposed row pass).
+    if (p->passes[0].blk == 1 && (reinterpret_cast<uintptr_t>(in) & 15) != 0)
+        d.blk = 0;
     auto buf = [&](int id) -> float2 * {
         return id == BUF_IN ? const_cast<float2 *>(static_cast<const float2 *>(in))
                             : (id == BUF_OUT ? static_cast<float2 *>(out) : p->workspace);
