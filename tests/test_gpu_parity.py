@@ -327,3 +327,41 @@ def test_eight_byte_aligned_buffers(env, shape, batch):
     ref = oracle_ref(env, x, list(shape), batch, -1)
     assert per_transform_rel(y, ref, batch).max() <= TOL
     assert per_transform_rel(yin.cpu().numpy(), ref, batch).max() <= TOL
+
+
+@pytest.mark.parametrize("shape,batch", [((1 << 24,), 1), ((4096, 4096), 1), ((256, 256, 256), 1), ((1 << 20,), 3)])
+def test_cuda_graph_of_dependent_launches(env, shape, batch):
+    """Execs whose passes are programmatic dependent launches, captured in a
+    CUDA graph (two execs back to back, so the second one's first pass
+    depends on the first one's last) and replayed twice, give the same bits
+    as the same execs run directly."""
+    torch, moafft, _ = env
+    from paper_0811_2535_gb300 import inputs
+    x = torch.from_numpy(inputs.uniform((batch,) + shape, 6700 + len(shape))).cuda()
+    plan = moafft.Plan(list(shape), batch, -1)
+    inv = moafft.Plan(list(shape), batch, 1)
+    y1, y2 = torch.empty_like(x), torch.empty_like(x)
+    plan.exec(x, y1)
+    inv.exec(y1, y2)
+    torch.cuda.synchronize()
+    ref1, ref2 = y1.clone(), y2.clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plan.exec(x, y1)
+        inv.exec(y1, y2)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.exec(x, y1)
+        inv.exec(y1, y2)
+    for _ in range(2):
+        y1.zero_()
+        y2.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(y1, ref1)
+        assert torch.equal(y2, ref2)
+    assert plan.status() == 0 and inv.status() == 0
+    plan.destroy()
+    inv.destroy()
