@@ -280,7 +280,6 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
 }  // namespace
 
 int batched_blocks_per_sm() { return kBlocksPerSM; }
-int batched_threads() { return kThreads; }
 
 cudaError_t launch_batched(const BatchLaunch &b, const float2 *in, float2 *out, int flags, cudaStream_t stream,
                            int *status)

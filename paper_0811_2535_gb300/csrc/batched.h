@@ -52,7 +52,6 @@ struct BatchLaunch {
 };
 
 int batched_blocks_per_sm();
-int batched_threads();
 cudaError_t launch_batched(const BatchLaunch &b, const float2 *in, float2 *out, int flags, cudaStream_t stream,
                            int *status);
 

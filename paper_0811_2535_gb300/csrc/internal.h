@@ -115,8 +115,6 @@ cudaError_t prepare_kernels();
 // Twiddle generation (FP64 on the device, rounded once to FP32).
 int stage_table_entries(int logN);
 cudaError_t generate_stage_table(float2 *dst, int logN, cudaStream_t stream);
-// dst[i] = w_modulus^(i*step mod modulus), i < count; sign -1.
-cudaError_t generate_powers(float2 *dst, int64_t count, int64_t step, int64_t modulus, cudaStream_t stream);
 // w_n^e for e < 2^h (lo) and w_n^(e*2^h) for e < n/2^h (hi); sign -1.
 cudaError_t generate_two_level(float2 *lo, float2 *hi, int logn, int h, cudaStream_t stream);
 

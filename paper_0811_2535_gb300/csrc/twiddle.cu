@@ -119,12 +119,6 @@ cudaError_t generate_full_stage(float2 *dst, int64_t M, int64_t M1, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t generate_powers(float2 *dst, int64_t count, int64_t step, int64_t modulus, cudaStream_t stream)
-{
-    power_table_kernel<<<(unsigned)((count + 255) / 256), 256, 0, stream>>>(dst, count, step, modulus);
-    return cudaGetLastError();
-}
-
 cudaError_t generate_two_level(float2 *lo, float2 *hi, int logn, int h, cudaStream_t stream)
 {
     const int64_t n = int64_t(1) << logn;
