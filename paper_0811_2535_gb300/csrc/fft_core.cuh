@@ -266,7 +266,9 @@ __device__ __forceinline__ int load_index(int r, int tau)
 }
 
 // Radix-R DFTs and twiddles of stage s on the registers of one thread.
-template <int LOGN, int s>
+// TWID = false leaves out the twiddles (a 2-D DFT whose slowest axis is the
+// stage-0 digit: the stage-0 DFT is then a transform of its own).
+template <int LOGN, int s, bool TWID = true>
 __device__ __forceinline__ void stage_compute(float2 (&v)[16], int tau, const float2 *__restrict__ tw)
 {
     using Sc = Sched<LOGN>;
@@ -276,7 +278,7 @@ __device__ __forceinline__ void stage_compute(float2 (&v)[16], int tau, const fl
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         dft<R>(&v[i * R]);
-        if constexpr (s != Sc::S - 1) {
+        if constexpr (TWID && s != Sc::S - 1) {
             const int b = tau + Sc::T * i;
             apply_twiddles<R>(&v[i * R], tw + Sc::tw_offset(s), b & (M1 - 1), M1);
         }

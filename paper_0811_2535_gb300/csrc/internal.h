@@ -11,8 +11,11 @@ enum PassKind {
     PASS_ROW = 0,
     PASS_COL = 1,
     PASS_TC = 2,
-    PASS_LIFT3 = 3   // fused second and third pass of a three-level lift (lift3.cu);
+    PASS_LIFT3 = 3,  // fused second and third pass of a three-level lift (lift3.cu);
                      // logF = log2 cA, logN = log2 cB
+    PASS_PLANE1 = 4, // 3-D 256^3, first of two passes: axis 2 and the first radix-16 step of
+                     // axis 1 (pass_kernels.cu); O = number of arrays
+    PASS_PLANE2 = 5  // 3-D 256^3, second pass: the rest of axis 1 and axis 0 (pipe_kernels.cu)
 };
 
 enum PassFlags {
@@ -66,6 +69,12 @@ bool encode_c64_map(CUtensorMap *map, const void *base, int rank, const uint64_t
 cudaError_t prepare_pipe_kernels();
 cudaError_t launch_pipe_pass(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
                              cudaStream_t stream, int *status);
+// The two passes of the two-pass 3-D transform of d.O arrays of 256^3: in ->
+// ws (w256[e] = w_256^e, e < 256), then ws -> out (ws 16-byte aligned).
+cudaError_t launch_plane1(const PassDesc &d, const float2 *in, float2 *ws, const TwiddleSet &tw, const float2 *w256,
+                          int flags, cudaStream_t stream);
+cudaError_t launch_pipe_plane2(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
+                               cudaStream_t stream, int *status);
 // Tensor-core rows (tc_kernels.cu): 1-D transforms of N = 256 or 4096 along
 // contiguous rows, radix-16 blocks as FP16 (hi/lo) or BF16 (hi/mid/lo) GEMMs.
 // `tw` holds the per-stage tables w_M^(u*k), k < 16 (tc_table_entries).

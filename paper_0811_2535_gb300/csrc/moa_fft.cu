@@ -49,6 +49,7 @@ struct moa_fft_plan_s {
     float2 *workspace = nullptr;
     size_t workspace_bytes = 0;
     int *d_status = nullptr;
+    const float2 *w256 = nullptr;  // two-pass 3-D: w_256^e, e < 256
     // choices an autotuner (or an override) may fix: -1 / 0 = default
     int opt_lr = -1;              // log2 r of a lifted 1-D transform
     int opt_pipe = -1;            // 0: generic kernels only, 1: pipelined strided kernels allowed
@@ -255,6 +256,31 @@ moa_status_t build_passes(moa_fft_plan_s *p)
         p->workspace_bytes = (size_t)p->total * sizeof(float2);
         return MOA_OK;
     }
+    // 3-D 256^3 in two passes (axis 1 lifted as 16 x 16): axis 2 and the
+    // first radix-16 step of axis 1, then the rest of axis 1 and axis 0; 32n
+    // bytes instead of the 48n of one pass per axis.  Needs the TMA kernels;
+    // MOA_3D_TWO_PASS=0 keeps one pass per axis.
+    const int pipe_mode = p->opt_pipe >= 0 ? p->opt_pipe : env_int("MOA_PIPE", 2);
+    if (p->dims == 3 && p->n[0] == 256 && p->n[1] == 256 && p->n[2] == 256 && pipe_mode > 0 &&
+        moa::pipe_supported() && env_int("MOA_3D_TWO_PASS", 1) != 0) {
+        PassDesc d1{};
+        d1.kind = moa::PASS_PLANE1;
+        d1.logN = 8;
+        d1.O = B;
+        d1.C = 1;
+        d1.Rt = 1;
+        d1.src = BUF_IN;
+        d1.dst = BUF_WS;
+        PassDesc d2 = d1;
+        d2.kind = moa::PASS_PLANE2;
+        d2.logN = 12;
+        d2.src = BUF_WS;
+        d2.dst = BUF_OUT;
+        p->passes.push_back(d1);
+        p->passes.push_back(d2);
+        p->workspace_bytes = (size_t)p->total * sizeof(float2);
+        return MOA_OK;
+    }
     // multi-D: last axis as rows, then every other axis as columns, in place
     const int d = p->dims;
     int src = BUF_IN;
@@ -378,6 +404,12 @@ moa_status_t allocate_and_fill(moa_fft_plan_s *p)
         hi_off = bytes;
         bytes += ((size_t(1) << (logn - h)) * sizeof(float2) + 255) & ~size_t(255);
     }
+    size_t w256_off = 0;
+    for (const PassDesc &d : p->passes)
+        if (d.kind == moa::PASS_PLANE1 && !w256_off) {
+            w256_off = bytes;
+            bytes += (257 * sizeof(float2) + 255) & ~size_t(255);
+        }
     size_t tc_off = 0;
     if (p->dtype != MOA_C64) {
         tc_off = bytes;
@@ -439,6 +471,12 @@ moa_status_t allocate_and_fill(moa_fft_plan_s *p)
         if (L == 12 && moa::generate_full_stage(t + 16 * 256, 256, 16, 0) != cudaSuccess)
             return MOA_ERR_CUDA;
         p->tw.tc = t;
+    }
+    if (w256_off) {
+        float2 *t = reinterpret_cast<float2 *>(base + w256_off);
+        if (moa::generate_two_level(t, t + 256, 8, 8, 0) != cudaSuccess)   // t[e] = w_256^e
+            return MOA_ERR_CUDA;
+        p->w256 = t;
     }
     if (p->split_r > 0) {
         float2 *lo = reinterpret_cast<float2 *>(base + lo_off);
@@ -704,6 +742,13 @@ moa_status_t run_pass(moa_fft_plan_s *p, size_t i, const void *in, void *out, cu
                                  p->d_status) == cudaSuccess
                    ? MOA_OK
                    : MOA_ERR_CUDA;
+    if (d.kind == moa::PASS_PLANE1)
+        return moa::launch_plane1(d, buf(d.src), buf(d.dst), p->tw, p->w256, flags, s) == cudaSuccess ? MOA_OK
+                                                                                                       : MOA_ERR_CUDA;
+    if (d.kind == moa::PASS_PLANE2)
+        return moa::launch_pipe_plane2(d, buf(d.src), buf(d.dst), p->tw, flags, s, p->d_status) == cudaSuccess
+                   ? MOA_OK
+                   : MOA_ERR_CUDA;
     if (d.kind == moa::PASS_TC) {
         const bool bf16 = p->dtype == MOA_C64_TC_BF16;
         const cudaError_t e = d.umma ? moa::launch_umma_pass(d, bf16, buf(d.src), buf(d.dst), p->tw.tc, flags, s,
@@ -884,6 +929,10 @@ void pass_name(const moa_fft_plan_s *p, const PassDesc &d, char *buf, size_t len
                  p->dtype == MOA_C64_TC_BF16 ? 1 : 0, d.logN);
     else if (d.kind == moa::PASS_LIFT3)
         snprintf(buf, len, "lift3_kernel<%d,%d>", d.logF, d.logN);
+    else if (d.kind == moa::PASS_PLANE1)
+        snprintf(buf, len, "plane3d_p1_kernel");
+    else if (d.kind == moa::PASS_PLANE2)
+        snprintf(buf, len, "pipe_col_kernel<12,0,3>");
     else if (d.pipe && (d.kind == moa::PASS_COL || d.blk == 2))
         snprintf(buf, len, "pipe_col_kernel<%d,%d,%d>", d.logN, d.tw4, d.blk);
     else if (d.pipe)

@@ -148,6 +148,63 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(const float2 *in, float2
     pdl_launch_dependents();
 }
 
+// First pass of the two-pass 3-D transform of 256 x 256 x 256 arrays.  Axis
+// 1 is lifted as j1 = j1a + 16*j1b (Sec. 4.2 applied to that axis).  Tile
+// (array o, plane j0, j1a): the 16 rows j1a + 16*j1b of the plane.  Their
+// 256-point transforms along axis 2 (16 threads per row), then, per column
+// k2 (one thread each), the 16-point DFT over j1b and the twiddle
+// w_256^(j1a*k1b); the result for k1b goes to row j1a + 16*k1b of the
+// workspace.  The second pass (the DFT over j1a and the axis-0 transform)
+// runs in pipe_col_kernel<12, false, 3>.
+__global__ void __launch_bounds__(256) plane3d_p1_kernel(const float2 *in, float2 *ws, int ntiles,
+                                                         const float2 *__restrict__ tw8,
+                                                         const float2 *__restrict__ w256, int flags)
+{
+    using Sc = Sched<8>;
+    static_assert(Sc::T == 16 && Sc::P == 16, "256-point rows, 16 threads per row");
+    __shared__ float2 sm[16 * (256 + 16)];   // the row exchange, then the 16 x 256 block
+    const int tid = threadIdx.x;
+    const int tile = blockIdx.x;
+    if (tile >= ntiles)
+        return;
+    const int j1a = tile & 15;
+    const int64_t plane = tile >> 4;   // o*256 + j0
+    const float2 *base = in + plane * 65536 + j1a * 256;
+
+    pdl_wait_prior();   // `in` may be the previous kernel's output, `ws` its input
+    const int f = tid >> 4, tau = tid & 15;   // row j1a + 16*f, 16 threads per row
+    float2 v[16];
+    const float2 *src = base + f * 4096 + tau;
+#pragma unroll
+    for (int q = 0; q < 16; ++q)   // radix 16 first: element tau + 16*q in register q
+        v[q] = src[q * 16];
+    if (flags & FLAG_CONJ_IN) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            v[q].y = -v[q].y;
+    }
+    fft_tile<8, -1>(v, sm, tau, f, tw8);   // v[k]: point tau + 16*k of row f's transform
+    // fft_tile's last exchange read is behind a block barrier: sm is free
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+        sm[f * 256 + tau + 16 * k] = v[k];
+    __syncthreads();
+    const int c = tid;   // column k2
+    float2 u[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+        u[j] = sm[j * 256 + c];
+    dft16(u);
+#pragma unroll
+    for (int k = 1; k < 16; ++k)
+        u[k] = cmul(u[k], __ldg(&w256[(j1a * k) & 255]));
+    float2 *dst = ws + plane * 65536 + j1a * 256 + c;
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+        dst[k * 4096] = u[k];
+    pdl_launch_dependents();   // after the stores
+}
+
 template <int LOGN>
 cudaError_t launch_typed(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
                          cudaStream_t stream)
@@ -187,6 +244,14 @@ cudaError_t set_attrs()
 }
 
 }  // namespace
+
+cudaError_t launch_plane1(const PassDesc &d, const float2 *in, float2 *ws, const TwiddleSet &tw, const float2 *w256,
+                          int flags, cudaStream_t stream)
+{
+    const int ntiles = (int)(d.O * 256 * 16);   // arrays x planes x j1a
+    return launch_maybe_dependent(plane3d_p1_kernel, (unsigned)ntiles, 256, 0, stream, flags & FLAG_PDL, in, ws,
+                                  ntiles, tw.stage[8], w256, flags);
+}
 
 int pass_threads(const PassDesc &d)
 {

@@ -137,12 +137,12 @@ __device__ __forceinline__ void bounded_wait(uint64_t *bar, uint32_t parity, int
 // The three radix stages of N = 1024, 2048, 4096 (radix 4/8/16, 16, 16) with
 // single-round exchanges through E; `after_last_read` runs once E is no
 // longer needed (used to start refilling it).
-template <int LOGN, typename F>
+template <int LOGN, bool TW0 = true, typename F>
 __device__ __forceinline__ void three_stages(float2 (&v)[16], float2 *E, int tau, int f, const float2 *__restrict__ tw,
                                              F after_last_read)
 {
     static_assert(Sched<LOGN>::S == 3, "three-stage schedule expected");
-    stage_compute<LOGN, 0>(v, tau, tw);
+    stage_compute<LOGN, 0, TW0>(v, tau, tw);
     stage_write<LOGN, 0, 2>(v, E, tau, f);
     __syncthreads();
     stage_read<LOGN, 1, 2>(v, E, tau, f);
@@ -169,6 +169,14 @@ __device__ __forceinline__ void three_stages(float2 (&v)[16], float2 *E, int tau
 //   BLK = 2: lifted pass 2 (N = c, C = r): the blocked workspace through a
 //            3-D tensor map {32 floats, r/4, O*c/4}, output in the [O][N][C]
 //            view, i.e. X[k1 + r*k2].
+//   BLK = 3: second pass of the two-pass 3-D transform of 256 x 256 x 256
+//            arrays (N = 4096, C = 256; the tile index within a transform is
+//            64*k1b + g): the 16 rows 16*k1b + j1a of every plane j0 and
+//            columns 4g..4g+3 land as element e = j0 + 256*j1a through a 3-D
+//            tensor map {512 floats, O*256 planes, 256 rows}.  The stage-0
+//            DFT (over j1a) takes no twiddle, so the tile computes the 2-D DFT
+//            over (j1a, j0); output k = k1a + 16*k0 goes to
+//            X[k0][k1b + 16*k1a][column].
 template <int LOGN, bool TW4, int BLK>
 __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
     pipe_col_kernel(const __grid_constant__ CUtensorMap tmap, float2 *out, int C, int logTpo, int ntiles,
@@ -197,7 +205,9 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
         const int r0 = h ? HR : 0, nb = (h ? N - HR : HR) / 256;
         mbar_arrive_expect_tx(b, nb * 256 * 4 * (uint32_t)sizeof(float2));
         for (int k = 0; k < nb; ++k) {
-            if constexpr (BLK == 2)
+            if constexpr (BLK == 3)
+                tma_load_3d(dst + k * 256 * 4, &tmap, b, 2 * (c0 & 255), o * 256, 16 * (c0 >> 8) + (r0 >> 8) + k);
+            else if constexpr (BLK == 2)
                 tma_load_3d(dst + k * 256 * 4, &tmap, b, 0, c0 >> 2, (o * N + r0 + k * 256) >> 2);
             else
                 tma_load_2d(dst + k * 256 * 4, &tmap, b, 2 * c0, o * N + r0 + k * 256);
@@ -258,7 +268,7 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
                 tk[tau * 4 + f] = two_level_tw(tw_lo, tw_hi, tw_h, (int64_t)col * (T * tau));
         }
 
-        three_stages<LOGN>(v, E, tau, f, tw, [&] {
+        three_stages<LOGN, BLK != 3>(v, E, tau, f, tw, [&] {
             if (tid == 0 && next < ntiles) {
                 fence_proxy_async();
                 issue_half(next, 1, E, &bar[1]);
@@ -276,7 +286,15 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
             for (int k = 0; k < 16; ++k)
                 v[k].y = -v[k].y;
         }
-        if constexpr (BLK == 1) {
+        if constexpr (BLK == 3) {
+            // output k = k1a + 16*k0 with tau + T*k = k: k1a = tau % 16, k0 = tau/16 + 16*k
+            static_assert(N == 4096 && T == 256, "the 3-D second pass is a 16 x 256 tile");
+            float2 *dst = out + ((int64_t)o << 24) + (int64_t)(tau >> 4) * 65536 +
+                          ((col >> 8) + 16 * (tau & 15)) * 256 + (col & 255);
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                dst[(int64_t)k << 20] = v[k];
+        } else if constexpr (BLK == 1) {
             // element (tau + T*k, col) of the tile: block ((col/4)*(N/4) + (tau + T*k)/4),
             // slot f*4 + tau%4 (T is a multiple of 4)
             float2 *dst = out + (int64_t)o * N * C + (int64_t)((col >> 2) * (N >> 2)) * 16 + f * 4 + (tau >> 2) * 16 +
@@ -476,6 +494,29 @@ cudaError_t launch_col(const PassDesc &d, int64_t O, int64_t C, int blk, const f
                                   ntiles, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags, status);
 }
 
+// Second pass of the two-pass 3-D transform of O arrays of 256^3 (BLK = 3).
+cudaError_t launch_plane2(int64_t O, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
+                          cudaStream_t stream, int *status)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc)
+        return cudaErrorNotSupported;
+    CUtensorMap map;
+    // {floats of one row, planes of all O arrays, rows of a plane}
+    const cuuint64_t dims[3] = {512, (cuuint64_t)(O * 256), 256};
+    const cuuint64_t strides[2] = {(cuuint64_t)65536 * sizeof(float2), (cuuint64_t)256 * sizeof(float2)};
+    const cuuint32_t box[3] = {8, 256, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2 *>(in), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    const int ntiles = (int)(O << 10);   // 16 row groups x 64 column groups per array
+    const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
+    return launch_maybe_dependent(pipe_col_kernel<12, false, 3>, grid, 1024, col_smem<12>(), stream, flags & FLAG_PDL,
+                                  map, out, 256, 10, ntiles, tw.stage[12], tw.lo, tw.hi, tw.h, flags, status);
+}
+
 template <int LOGN>
 cudaError_t launch_rowT(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
                         cudaStream_t stream, int *status)
@@ -534,7 +575,16 @@ cudaError_t prepare_pipe_kernels()
         return e;
     if ((e = set_pipe_attrs<10>()) || (e = set_pipe_attrs<11>()) || (e = set_pipe_attrs<12>()))
         return e;
+    if ((e = cudaFuncSetAttribute(pipe_col_kernel<12, false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)col_smem<12>())))
+        return e;
     return cudaSuccess;
+}
+
+cudaError_t launch_pipe_plane2(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
+                               cudaStream_t stream, int *status)
+{
+    return launch_plane2(d.O, in, out, tw, flags, stream, status);
 }
 
 cudaError_t launch_pipe_pass(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,

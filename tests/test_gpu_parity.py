@@ -365,3 +365,26 @@ def test_cuda_graph_of_dependent_launches(env, shape, batch):
     assert plan.status() == 0 and inv.status() == 0
     plan.destroy()
     inv.destroy()
+
+
+@pytest.mark.parametrize("batch", [1, 2])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_3d_two_pass(env, batch, sign, monkeypatch):
+    """256^3 in two passes (axis 1 lifted as 16 x 16): against the oracle,
+    against one pass per axis (MOA_3D_TWO_PASS=0), and in place."""
+    torch, moafft, _ = env
+    from paper_0811_2535_gb300 import inputs
+    shape = (256, 256, 256)
+    x = inputs.uniform((batch,) + shape, 6800 + batch)
+    plan = moafft.Plan(list(shape), batch, sign)
+    names = [plan.pass_info(i)["kernel"] for i in range(plan.info()["passes"])]
+    plan.destroy()
+    assert names == ["plane3d_p1_kernel", "pipe_col_kernel<12,0,3>"], names
+    y, _ = run(env, list(shape), batch, sign, x)
+    yi, _ = run(env, list(shape), batch, sign, x, inplace=True)
+    monkeypatch.setenv("MOA_3D_TWO_PASS", "0")
+    y3, _ = run(env, list(shape), batch, sign, x)
+    ref = oracle_ref(env, x, list(shape), batch, sign)
+    assert per_transform_rel(y, ref, batch).max() <= TOL
+    assert np.array_equal(y, yi)
+    assert per_transform_rel(y3, ref, batch).max() <= TOL
