@@ -20,6 +20,14 @@ Which passage each function follows:
 * :func:`fft_nd`         -- Appendix B, Eq. B.6 (Omega along each axis).
 * :func:`gamma`          -- Appendix A, Definition A.1 (row-major offset).
 
+The paper's shared-memory all-processor templates, run on the host cores
+(``fft_template.c``, OpenMP where gcc has it), are the CPU comparison point
+for the GPU path; their results equal the sequential plans bit for bit:
+
+* :func:`template_partitioned` -- Sec. 6.3, Fig. 6.4 (both p loops parallel).
+* :func:`template_nd`          -- Eq. B.6 with the lines of each axis in
+  parallel.
+
 Every function is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_pins.py`` against brute force, closed forms, invariants
 and the worked example of Appendix A.
@@ -36,6 +44,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fft_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
+_TSRC = os.path.join(_HERE, "fft_template.c")
+_TLIB = os.path.join(_HERE, "libtemplate.so")
+_tlib = None
 
 
 def build(force: bool = False) -> str:
@@ -46,6 +57,35 @@ def build(force: bool = False) -> str:
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_template(force: bool = False) -> str:
+    """Compile ``fft_template.c`` into ``libtemplate.so``: with OpenMP where the
+    compiler accepts ``-fopenmp``, else as plain sequential C."""
+    if force or not os.path.exists(_TLIB) or os.path.getmtime(_TLIB) < os.path.getmtime(_TSRC):
+        tmp = _TLIB + f".tmp{os.getpid()}"
+        base = ["gcc", "-O2", "-std=c11", "-fno-fast-math", "-shared", "-fPIC", "-o", tmp, _TSRC, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except (subprocess.CalledProcessError, OSError):
+            subprocess.check_call(base)
+        os.replace(tmp, _TLIB)
+    return _TLIB
+
+
+def _load_template():
+    global _tlib
+    if _tlib is None:
+        lib = ctypes.CDLL(build_template())
+        dp = ctypes.POINTER(ctypes.c_double)
+        i64 = ctypes.c_int64
+        lib.tmpl_fft_partitioned.argtypes = [dp, i64, i64, ctypes.c_int, ctypes.c_int]
+        lib.tmpl_fft_nd.argtypes = [dp, ctypes.POINTER(i64), ctypes.c_int, i64, ctypes.c_int]
+        lib.tmpl_max_threads.argtypes = []
+        for f in ("tmpl_fft_partitioned", "tmpl_fft_nd", "tmpl_max_threads"):
+            getattr(lib, f).restype = ctypes.c_int
+        _tlib = lib
+    return _tlib
 
 
 def _load():
@@ -144,3 +184,30 @@ def psi(a: np.ndarray, index) -> np.ndarray:
     start = gamma(shape, list(index) + [0] * (len(shape) - k))
     out = flat[start:start + count]
     return out.reshape(rest) if rest else out[0]
+
+
+def template_threads() -> int:
+    """Threads the parallel loops of the templates use (1 without OpenMP)."""
+    return int(_load_template().tmpl_max_threads())
+
+
+def template_partitioned(x, m: int, breakpoint: int, sign: int = -1) -> np.ndarray:
+    """Fig. 6.4: the Fig. 4.9 plan with both p loops run in parallel (1-D)."""
+    y = _c128(x).copy()
+    _check(_load_template().tmpl_fft_partitioned(_ptr(y), y.size, m, breakpoint, sign),
+           "template_partitioned")
+    return y
+
+
+def template_nd(x, dims: int, sign: int = -1, inplace: bool = False) -> np.ndarray:
+    """Eq. B.6 over the last ``dims`` axes with the lines of each axis run in
+    parallel; leading axes are the batch.  ``inplace`` transforms a contiguous
+    complex128 ``x`` itself."""
+    y = x if inplace else _c128(x).copy()
+    if inplace and not (y.dtype == np.complex128 and y.flags.c_contiguous):
+        raise ValueError("inplace needs a contiguous complex128 array")
+    shape = y.shape[y.ndim - dims:]
+    batch = int(np.prod(y.shape[:y.ndim - dims], dtype=np.int64)) if y.ndim > dims else 1
+    sh = (ctypes.c_int64 * dims)(*shape)
+    _check(_load_template().tmpl_fft_nd(_ptr(y), sh, dims, batch, sign), "template_nd")
+    return y

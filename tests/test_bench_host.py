@@ -29,3 +29,13 @@ def test_kernel_hash_ignores_comments_only():
     h = bench.kernel_src_hash("pipe_col_kernel<12,1,1>")
     assert len(h) == 16 and h == bench.kernel_src_hash("pipe_col_kernel<12,0,2>")
     assert h != bench.kernel_src_hash("row_pass_kernel<12,0>")
+
+
+def test_template_step_small_workload_equals_oracle():
+    """The CPU comparison leg on a small step: every output equals the
+    sequential oracle's, and the 1-D processor count stays a power of two
+    with m * m <= n."""
+    import bench
+    secs, threads, m, same = bench.template_step([(1 << 12,), (64, 32), (16, 8, 4)], 1, reps=1)
+    assert same and secs > 0 and threads >= 1
+    assert m >= 1 and (m & (m - 1)) == 0 and m <= threads and m * m <= 1 << 12
