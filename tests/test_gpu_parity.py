@@ -388,3 +388,39 @@ def test_3d_two_pass(env, batch, sign, monkeypatch):
     assert per_transform_rel(y, ref, batch).max() <= TOL
     assert np.array_equal(y, yi)
     assert per_transform_rel(y3, ref, batch).max() <= TOL
+
+
+@pytest.mark.parametrize("shape", [(1 << 24,), (4096, 4096), (256, 256, 256)])
+def test_largest_plan(env, shape, monkeypatch):
+    """The largest plan the library accepts: 127 transforms of 2^24 points
+    (2^31 - 2^24 elements, 17 GB per buffer), so that element offsets above
+    2^31 occur in every pass.  Transform b is the seeded full-size input rolled
+    by 7919*b and scaled by 2^(b % 8 - 4) (exact in FP32).  Transforms 1 and 126
+    are compared element by element with the oracle; every transform is checked
+    by Parseval against its own input energy, which a transform written to a
+    neighbour's place fails (the neighbours' scales differ by 2x)."""
+    torch, moafft, _ = env
+    from paper_0811_2535_gb300 import inputs
+    monkeypatch.setenv("MOA_AUTOTUNE", "0")
+    n, B = int(np.prod(shape)), 127
+    base = inputs.uniform(shape, inputs.SEED_LARGE).reshape(-1)
+    base_d = torch.from_numpy(base).cuda()
+    x = torch.empty((B, n), dtype=torch.complex64, device="cuda")
+    for b in range(B):
+        x[b] = torch.roll(base_d, 7919 * b) * (2.0 ** (b % 8 - 4))
+    plan = moafft.Plan(list(shape), B, -1)
+    y = plan.exec(x)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    plan.destroy()
+    for b in range(B):
+        ex = float(torch.sum(torch.abs(x[b]).double() ** 2))
+        ey = float(torch.sum(torch.abs(y[b]).double() ** 2))
+        assert abs(ey / (n * ex) - 1.0) < 1e-5, (b, ey / (n * ex))
+    for b in (1, B - 1):
+        xb = (np.roll(base, 7919 * b) * np.float32(2.0 ** (b % 8 - 4))).astype(np.complex64)
+        yb = y[b].cpu().numpy()
+        ref = oracle_ref(env, xb, list(shape), 1, -1)
+        assert per_transform_rel(yb, ref, 1).max() <= TOL, b
+    del x, y
+    torch.cuda.empty_cache()
