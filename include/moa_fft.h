@@ -169,6 +169,32 @@ MOA_API moa_status_t moa_fft_plan_info(moa_fft_plan_t plan, int *passes, int64_t
 MOA_API moa_status_t moa_fft_pass_info(moa_fft_plan_t plan, int index, char *name, size_t name_len,
                                        int64_t *bytes);
 
+/* Host-only estimate of the plan moa_fft_plan would build for the same
+ * request with the autotuner off (MOA_AUTOTUNE=0): the passes (the dimension
+ * lifting n = r*c of Sec. 4.2 for a 1-D transform, the r x c split chosen as
+ * the breakpoint of Sec. 4.8; one pass per axis, Eq. B.6, or the two-pass
+ * 256^3 form for multi-D), the kernel each pass launches and the workspace
+ * size, without touching the GPU and without allocating device memory.  The
+ * environment overrides the plan reads (MOA_SPLIT_LOG2R, MOA_PIPE,
+ * MOA_LIFT3, MOA_3D_TWO_PASS, MOA_TC_KERNEL) apply here too.
+ *   n, dims, batch, dtype : as for moa_fft_plan (same checks, same error
+ *                           codes; the sign does not change the plan).
+ *   tma    : 1 = assume the driver's tensor-map encoder is present (the
+ *            pipelined TMA kernels may be chosen, as on any GB300 driver),
+ *            0 = assume it is absent (generic kernels only), -1 = ask the
+ *            driver.
+ *   passes, split_r, split_c, workspace_bytes : as moa_fft_plan_info
+ *            reports them; any may be NULL.
+ *   kernels: the kernel names of the passes, in order, separated by ';'
+ *            (the names moa_fft_pass_info reports), NUL-terminated and
+ *            truncated to kernels_len - 1 characters; may be NULL when
+ *            kernels_len is 0.
+ * Returns MOA_ERR_INVALID_ARG for tma outside {-1, 0, 1} or a NULL kernels
+ * buffer with kernels_len > 0. */
+MOA_API moa_status_t moa_fft_estimate(const int64_t *n, int dims, int64_t batch, int dtype, int tma,
+                                      int *passes, int64_t *split_r, int64_t *split_c,
+                                      size_t *workspace_bytes, char *kernels, size_t kernels_len);
+
 /* Destroy a plan and free everything it owns.  NULL is a no-op (MOA_OK);
  * a handle that is not a live plan returns MOA_ERR_INVALID_ARG. */
 MOA_API moa_status_t moa_fft_destroy(moa_fft_plan_t plan);

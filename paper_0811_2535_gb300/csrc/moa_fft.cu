@@ -55,6 +55,7 @@ struct moa_fft_plan_s {
     int opt_pipe = -1;            // 0: generic kernels only, 1: pipelined strided kernels allowed
     int opt_batch_dlr = 0;        // batched: log2 r offset from floor(log2 n / 2)
     int opt_lift3 = -1;           // 1-D: 1 = three-level lift (r = 256, fused second/third pass)
+    bool tma = false;             // tensor-map encoder present: pipelined kernels and the two-pass 3-D plan allowed
     moa::Lift3Launch l3{};
     void *l3_block = nullptr;     // two-level table of w_c, task queue, ticket and unit counters
     // batched plans (moa_fft_plan_batched): one persistent launch
@@ -261,8 +262,8 @@ moa_status_t build_passes(moa_fft_plan_s *p)
     // bytes instead of the 48n of one pass per axis.  Needs the TMA kernels;
     // MOA_3D_TWO_PASS=0 keeps one pass per axis.
     const int pipe_mode = p->opt_pipe >= 0 ? p->opt_pipe : env_int("MOA_PIPE", 2);
-    if (p->dims == 3 && p->n[0] == 256 && p->n[1] == 256 && p->n[2] == 256 && pipe_mode > 0 &&
-        moa::pipe_supported() && env_int("MOA_3D_TWO_PASS", 1) != 0) {
+    if (p->dims == 3 && p->n[0] == 256 && p->n[1] == 256 && p->n[2] == 256 && pipe_mode > 0 && p->tma &&
+        env_int("MOA_3D_TWO_PASS", 1) != 0) {
         PassDesc d1{};
         d1.kind = moa::PASS_PLANE1;
         d1.logN = 8;
@@ -294,6 +295,31 @@ moa_status_t build_passes(moa_fft_plan_s *p)
         p->passes.push_back(col_pass(ilog2(p->n[a]), outer, inner, 0, BUF_OUT, BUF_OUT));
     }
     return MOA_OK;
+}
+
+// Which strided passes run in the pipelined TMA kernels.  They need the
+// tensor-map encoder; without it the plan keeps the generic kernels (same
+// results, slower).  MOA_PIPE=0 forces the generic kernels (tests compare
+// both paths), MOA_PIPE=1 keeps them but without the blocked workspace.
+void assign_pipe(moa_fft_plan_s *p)
+{
+    const int pipe_mode = p->tma ? (p->opt_pipe >= 0 ? p->opt_pipe : env_int("MOA_PIPE", 2)) : 0;
+    for (PassDesc &d : p->passes) {
+        const bool strided4 = d.logN >= 10 && d.logN <= 12 && d.logF == 2 &&
+                              (d.kind == moa::PASS_COL ? d.C >= 4 : d.Rt > 1);
+        d.pipe = 0;
+        d.blk = 0;
+        if (strided4 && pipe_mode > 0)
+            d.pipe = 1;
+    }
+    // lifted 1-D with both passes pipelined: the intermediate goes through
+    // the workspace as 4 x 4 blocks (whole-block stores in pass 1, whole-block
+    // loads in pass 2 instead of 32-byte segments)
+    if (pipe_mode >= 2 && p->dims == 1 && p->passes.size() == 2 && p->passes[0].pipe && p->passes[1].pipe &&
+        p->passes[0].kind == moa::PASS_COL && p->passes[0].tw4 && p->passes[1].kind == moa::PASS_ROW) {
+        p->passes[0].blk = 1;
+        p->passes[1].blk = 2;
+    }
 }
 
 // Device block of the fused second/third pass of a three-level lift: the
@@ -433,28 +459,6 @@ moa_status_t allocate_and_fill(moa_fft_plan_s *p)
         return MOA_ERR_CUDA;
     if (moa::prepare_pipe_kernels() != cudaSuccess)
         return MOA_ERR_CUDA;
-    // the pipelined strided kernels need the tensor-map encoder; without it
-    // the plan keeps the generic kernels (same results, slower)
-    // MOA_PIPE=0 forces the generic kernels (tests compare both paths)
-    // MOA_PIPE=1 keeps them but without the blocked workspace
-    const int pipe_mode =
-        moa::pipe_supported() ? (p->opt_pipe >= 0 ? p->opt_pipe : env_int("MOA_PIPE", 2)) : 0;
-    for (PassDesc &d : p->passes) {
-        const bool strided4 = d.logN >= 10 && d.logN <= 12 && d.logF == 2 &&
-                              (d.kind == moa::PASS_COL ? d.C >= 4 : d.Rt > 1);
-        d.pipe = 0;
-        d.blk = 0;
-        if (strided4 && pipe_mode > 0)
-            d.pipe = 1;
-    }
-    // lifted 1-D with both passes pipelined: the intermediate goes through
-    // the workspace as 4 x 4 blocks (whole-block stores in pass 1, whole-block
-    // loads in pass 2 instead of 32-byte segments)
-    if (pipe_mode >= 2 && p->dims == 1 && p->passes.size() == 2 && p->passes[0].pipe && p->passes[1].pipe &&
-        p->passes[0].kind == moa::PASS_COL && p->passes[0].tw4 && p->passes[1].kind == moa::PASS_ROW) {
-        p->passes[0].blk = 1;
-        p->passes[1].blk = 2;
-    }
     for (int l = 1; l <= 12; ++l) {
         p->tw.stage[l] = nullptr;
         if (offs[l]) {
@@ -987,9 +991,12 @@ moa_status_t make_plan(moa_fft_plan_s **out, const int64_t *n, int dims, int64_t
     p->opt_lr = opt_lr;
     p->opt_pipe = opt_pipe;
     p->opt_lift3 = opt_lift3;
+    p->tma = moa::pipe_supported();
     moa_status_t st = build_passes(p);
-    if (st == MOA_OK)
+    if (st == MOA_OK) {
+        assign_pipe(p);
         st = allocate_and_fill(p);
+    }
     if (st != MOA_OK) {
         free_plan_memory(p);
         delete p;
@@ -1021,6 +1028,31 @@ moa_status_t make_batched(moa_fft_plan_s **out, const int64_t *lengths, int64_t 
 
 }  // namespace
 
+// Argument checks shared by moa_fft_plan and moa_fft_estimate; *total gets
+// the complex elements per exec.
+moa_status_t validate_request(const int64_t *n, int dims, int64_t batch, int sign, int dtype, int64_t *total)
+{
+    if (!n || dims < 1 || dims > 3 || batch < 1 || (sign != 1 && sign != -1))
+        return MOA_ERR_INVALID_ARG;
+    if (dtype != MOA_C64 && dtype != MOA_C64_TC_FP16 && dtype != MOA_C64_TC_BF16)
+        return MOA_ERR_INVALID_ARG;
+    int64_t t = batch;
+    for (int i = 0; i < dims; ++i) {
+        if (!pow2_ge2(n[i]))
+            return MOA_ERR_INVALID_SIZE;
+        if (dims == 1 ? n[i] > (int64_t(1) << 24) : n[i] > 4096)
+            return MOA_ERR_UNSUPPORTED;
+        t *= n[i];
+        if (t >= (int64_t(1) << 31))
+            return MOA_ERR_UNSUPPORTED;
+    }
+    // the tensor-core path covers 1-D transforms of 256 or 4096 points
+    if (dtype != MOA_C64 && !(dims == 1 && (n[0] == 256 || n[0] == 4096)))
+        return MOA_ERR_UNSUPPORTED;
+    *total = t;
+    return MOA_OK;
+}
+
 extern "C" {
 
 moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int64_t batch, int sign, int dtype)
@@ -1028,23 +1060,9 @@ moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int6
     if (!plan)
         return MOA_ERR_INVALID_ARG;
     *plan = nullptr;
-    if (!n || dims < 1 || dims > 3 || batch < 1 || (sign != 1 && sign != -1))
-        return MOA_ERR_INVALID_ARG;
-    if (dtype != MOA_C64 && dtype != MOA_C64_TC_FP16 && dtype != MOA_C64_TC_BF16)
-        return MOA_ERR_INVALID_ARG;
-    int64_t total = batch;
-    for (int i = 0; i < dims; ++i) {
-        if (!pow2_ge2(n[i]))
-            return MOA_ERR_INVALID_SIZE;
-        if (dims == 1 ? n[i] > (int64_t(1) << 24) : n[i] > 4096)
-            return MOA_ERR_UNSUPPORTED;
-        total *= n[i];
-        if (total >= (int64_t(1) << 31))
-            return MOA_ERR_UNSUPPORTED;
-    }
-    // the tensor-core path covers 1-D transforms of 256 or 4096 points
-    if (dtype != MOA_C64 && !(dims == 1 && (n[0] == 256 || n[0] == 4096)))
-        return MOA_ERR_UNSUPPORTED;
+    int64_t total = 0;
+    if (const moa_status_t vs = validate_request(n, dims, batch, sign, dtype, &total))
+        return vs;
 
     int opt_lr = -1, opt_pipe = -1, opt_lift3 = -1;
     const int L = ilog2(n[0]);
@@ -1301,6 +1319,47 @@ moa_status_t moa_fft_pass_info(moa_fft_plan_t plan, int index, char *name, size_
     }
     if (bytes)
         *bytes = 2 * (int64_t)sizeof(float2) * plan->total;
+    return MOA_OK;
+}
+
+moa_status_t moa_fft_estimate(const int64_t *n, int dims, int64_t batch, int dtype, int tma, int *passes,
+                              int64_t *split_r, int64_t *split_c, size_t *workspace_bytes, char *kernels,
+                              size_t kernels_len)
+{
+    if (tma < -1 || tma > 1 || (kernels_len > 0 && !kernels))
+        return MOA_ERR_INVALID_ARG;
+    int64_t total = 0;
+    if (const moa_status_t vs = validate_request(n, dims, batch, -1, dtype, &total))
+        return vs;
+    moa_fft_plan_s p;   // host description only: nothing is allocated or launched
+    p.dims = dims;
+    for (int i = 0; i < dims; ++i)
+        p.n[i] = n[i];
+    p.batch = batch;
+    p.dtype = dtype;
+    p.total = total;
+    p.tma = tma < 0 ? moa::pipe_supported() : tma == 1;
+    if (const moa_status_t st = build_passes(&p))
+        return st;
+    assign_pipe(&p);
+    if (passes)
+        *passes = (int)p.passes.size();
+    if (split_r)
+        *split_r = p.split_r;
+    if (split_c)
+        *split_c = p.split_c;
+    if (workspace_bytes)
+        *workspace_bytes = p.workspace_bytes;
+    if (kernels_len > 0) {
+        std::string all;
+        for (size_t i = 0; i < p.passes.size(); ++i) {
+            char buf[64];
+            pass_name(&p, p.passes[i], buf, sizeof(buf));
+            all += (i ? ";" : "") + std::string(buf);
+        }
+        strncpy(kernels, all.c_str(), kernels_len - 1);
+        kernels[kernels_len - 1] = '\0';
+    }
     return MOA_OK;
 }
 

@@ -41,6 +41,9 @@ SIGNATURES = {
     "moa_fft_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64),
                                          ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_size_t)]),
     "moa_fft_pass_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(_I64)]),
+    "moa_fft_estimate": (ctypes.c_int, [ctypes.POINTER(_I64), ctypes.c_int, _I64, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                        ctypes.POINTER(ctypes.c_size_t), ctypes.c_char_p, ctypes.c_size_t]),
     "moa_fft_destroy": (ctypes.c_int, [_P]),
 }
 
@@ -66,6 +69,21 @@ def lib() -> ctypes.CDLL:
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+def estimate(shape: Sequence[int], batch: int = 1, dtype: int = MOA_C64, tma: int = -1) -> dict:
+    """Host-only description of the plan for ``shape`` x ``batch`` with the
+    autotuner off (``moa_fft_estimate``): passes, r x c split, workspace bytes
+    and the kernel of each pass.  ``tma``: 1 / 0 assume the tensor-map encoder
+    present / absent, -1 asks the driver.  Needs no GPU."""
+    arr = (_I64 * len(shape))(*[int(v) for v in shape])
+    np_, r, c, ws = ctypes.c_int(), _I64(), _I64(), ctypes.c_size_t()
+    buf = ctypes.create_string_buffer(512)
+    _check(lib().moa_fft_estimate(arr, len(shape), int(batch), int(dtype), int(tma), ctypes.byref(np_),
+                                  ctypes.byref(r), ctypes.byref(c), ctypes.byref(ws), buf, len(buf)),
+           "moa_fft_estimate")
+    return {"passes": np_.value, "split_r": r.value, "split_c": c.value, "workspace_bytes": ws.value,
+            "kernels": buf.value.decode().split(";") if buf.value else []}
 
 
 def error_string(code: int) -> str:

@@ -98,3 +98,21 @@ def test_plan_log(env, tmp_path):
     assert len(plan_lines) == 2, lines
     assert "131072 batch 2 sign -1" in plan_lines[0] and "autotuned" in plan_lines[0]
     assert "64x32 batch 1 sign +1" in plan_lines[1] and "row_pass_kernel<5,0> -> col_pass_kernel<6,0>" in plan_lines[1]
+
+
+@pytest.mark.parametrize("shape,batch,dtype", [((1 << 24,), 1, 0), ((1 << 19,), 2, 0), ((1 << 13,), 3, 0),
+                                               ((1 << 10,), 4, 0), ((4096, 4096), 1, 0), ((256, 256, 256), 1, 0),
+                                               ((8, 16, 32), 2, 0), ((4096,), 8, 1), ((256,), 8, 2)])
+def test_estimate_matches_the_plan(env, shape, batch, dtype, monkeypatch):
+    """moa_fft_estimate, asking the driver (tma = -1), describes exactly the
+    plan moa_fft_plan builds with the autotuner off."""
+    _, moafft, _ = env
+    monkeypatch.setenv("MOA_AUTOTUNE", "0")
+    e = moafft.estimate(list(shape), batch, dtype=dtype, tma=-1)
+    plan = moafft.Plan(list(shape), batch, -1, dtype)
+    info = plan.info()
+    kernels = [plan.pass_info(i)["kernel"] for i in range(info["passes"])]
+    plan.destroy()
+    assert e["kernels"] == kernels
+    assert (e["passes"], e["split_r"], e["split_c"], e["workspace_bytes"]) == \
+        (info["passes"], info["split_r"], info["split_c"], info["workspace_bytes"])
