@@ -10,13 +10,14 @@
 // computed, shared memory its exchange buffer).  To keep HBM busy anyway
 // each block is persistent and refills its shared memory asynchronously:
 //
-//   H (first-half landing buffer, N/2 x 4 complex64): TMA brings the first
-//     half of tile i+1 (cp.async.bulk.tensor 2-D boxes of 256 rows x 32 bytes
-//     for columns, 1-D cp.async.bulk copies for rows) while tile i computes;
+//   H (landing buffer): TMA brings the first part of tile i+1 while tile i
+//     computes: for columns, as many 256-row boxes (cp.async.bulk.tensor,
+//     256 rows x 32 bytes) as fit beside E, 11 of 16 at N = 4096; for rows,
+//     the first half of each row (cp.async.bulk);
 //   E (exchange buffer, (N + N/16) x 4 complex64): the single-round register
 //     exchanges of tile i's radix-16 stages; as soon as the last exchange has
-//     been read, TMA lands the second half of tile i+1 in it, overlapping the
-//     last stage, the epilogue and the stores of tile i.
+//     been read, TMA lands the rest of tile i+1 in it, overlapping the last
+//     stage, the epilogue and the stores of tile i.
 //
 // Completion is tracked on two mbarriers.  One elected thread waits on them
 // with an iteration limit; on timeout it records MOA_ERR_TIMEOUT in the
