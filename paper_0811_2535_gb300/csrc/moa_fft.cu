@@ -9,9 +9,16 @@
 //     (block phase), then a row pass of c-point transforms whose store
 //     performs the transpose X[k1 + r*k2] (cyclic phase).  Any r*c split
 //     is correct (Sec. 4.8); the default is r = 2^floor(t/2).
+//     For n = 2^21..2^24 the rows may be lifted once more, c = cA*cB, in
+//     one fused launch (three-level lift, lift3.cu), where the autotuner
+//     finds it faster.
 //   * 2-D / 3-D: the 1-D transform applied along every axis (Omega,
 //     Appendix B, Eq. B.6): a row pass on the last axis, column passes on
-//     the others.
+//     the others; 256^3 arrays in two passes instead, with axis 1 lifted as
+//     16 x 16 (plane3d_p1_kernel, then pipe_col_kernel<12,0,3>).
+// The autotuner (the paper's script-based search) times the admissible
+// choices of a 1-D plan; moa_fft_estimate describes the default plan on the
+// host without a GPU.
 #include <cuda_runtime.h>
 
 #include <cstdio>
