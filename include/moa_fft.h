@@ -169,6 +169,27 @@ MOA_API moa_status_t moa_fft_plan_info(moa_fft_plan_t plan, int *passes, int64_t
 MOA_API moa_status_t moa_fft_pass_info(moa_fft_plan_t plan, int index, char *name, size_t name_len,
                                        int64_t *bytes);
 
+/* Copy one of the plan's twiddle tables to host memory, for tests and
+ * diagnostics: each entry is w_M^e = exp(-2 pi i e / M) evaluated once in
+ * FP64 on the device (exact reduction e mod M, Fig. 3.8: weights computed
+ * directly, not by recurrence) and rounded once to complex64.
+ *   table 0: the stage table of the 2^index-point in-register transform
+ *            (index 1..12, present when a pass of the plan uses it and it
+ *            is not empty): for every radix stage s but the last, six rows
+ *            k = 1, 2, 3, 4, 8, 12 of w_M^(u*k), u < M1 (M the stage's
+ *            span, M1 = M / radix), row after row, stage after stage;
+ *   table 1: lo[i] = w_n^i, i < 2^h, and
+ *   table 2: hi[j] = w_n^(j * 2^h), j < n / 2^h: the two halves of the
+ *            four-step twiddle w_n^e = lo[e mod 2^h] * hi[e / 2^h] of a
+ *            lifted 1-D plan of length n (present when the plan lifts).
+ *   host_out : caller-owned host memory of `capacity` complex64 entries;
+ *              NULL with capacity 0 only reports *entries.
+ *   entries  : receives the table's length (may be NULL).
+ * Synchronous.  MOA_ERR_INVALID_ARG for a dead or batched plan, a table the
+ * plan does not hold, or capacity below the length. */
+MOA_API moa_status_t moa_fft_plan_table(moa_fft_plan_t plan, int table, int index, void *host_out,
+                                        int64_t capacity, int64_t *entries);
+
 /* Host-only estimate of the plan moa_fft_plan would build for the same
  * request with the autotuner off (MOA_AUTOTUNE=0): the passes (the dimension
  * lifting n = r*c of Sec. 4.2 for a 1-D transform, the r x c split chosen as

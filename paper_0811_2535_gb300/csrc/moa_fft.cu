@@ -1329,6 +1329,38 @@ moa_status_t moa_fft_pass_info(moa_fft_plan_t plan, int index, char *name, size_
     return MOA_OK;
 }
 
+moa_status_t moa_fft_plan_table(moa_fft_plan_t plan, int table, int index, void *host_out, int64_t capacity,
+                                int64_t *entries)
+{
+    if (!is_live(plan) || plan->batched)
+        return MOA_ERR_INVALID_ARG;
+    const float2 *src = nullptr;
+    int64_t count = 0;
+    if (table == 0) {
+        if (index < 1 || index > 12 || !plan->tw.stage[index])
+            return MOA_ERR_INVALID_ARG;
+        src = plan->tw.stage[index];
+        count = moa::stage_table_entries(index);
+    } else if (table == 1 || table == 2) {
+        if (!plan->tw.lo || !plan->tw.hi)
+            return MOA_ERR_INVALID_ARG;
+        const int logn = ilog2(plan->total / plan->batch);
+        src = table == 1 ? plan->tw.lo : plan->tw.hi;
+        count = table == 1 ? (int64_t(1) << plan->tw.h) : (int64_t(1) << (logn - plan->tw.h));
+    } else {
+        return MOA_ERR_INVALID_ARG;
+    }
+    if (entries)
+        *entries = count;
+    if (!host_out)
+        return capacity == 0 ? MOA_OK : MOA_ERR_INVALID_ARG;
+    if (capacity < count)
+        return MOA_ERR_INVALID_ARG;
+    if (count > 0 && cudaMemcpy(host_out, src, (size_t)count * sizeof(float2), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return MOA_ERR_CUDA;
+    return MOA_OK;
+}
+
 moa_status_t moa_fft_estimate(const int64_t *n, int dims, int64_t batch, int dtype, int tma, int *passes,
                               int64_t *split_r, int64_t *split_c, size_t *workspace_bytes, char *kernels,
                               size_t kernels_len)

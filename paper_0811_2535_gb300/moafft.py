@@ -44,6 +44,7 @@ SIGNATURES = {
     "moa_fft_estimate": (ctypes.c_int, [ctypes.POINTER(_I64), ctypes.c_int, _I64, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                         ctypes.POINTER(ctypes.c_size_t), ctypes.c_char_p, ctypes.c_size_t]),
+    "moa_fft_plan_table": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _I64, ctypes.POINTER(_I64)]),
     "moa_fft_destroy": (ctypes.c_int, [_P]),
 }
 
@@ -179,6 +180,19 @@ class Plan:
         b = _I64()
         _check(lib().moa_fft_pass_info(self._h, int(index), buf, 64, ctypes.byref(b)), "moa_fft_pass_info")
         return {"kernel": buf.value.decode(), "bytes": b.value}
+
+    def table(self, which: int, index: int = 0):
+        """Copy of twiddle table ``which`` (0: stage table of 2^index points,
+        1 / 2: low / high half of the four-step twiddle) as a complex64 numpy
+        array (``moa_fft_plan_table``)."""
+        import numpy as np
+        count = _I64()
+        _check(lib().moa_fft_plan_table(self._h, int(which), int(index), None, 0, ctypes.byref(count)),
+               "moa_fft_plan_table")
+        out = np.empty(count.value, dtype=np.complex64)
+        _check(lib().moa_fft_plan_table(self._h, int(which), int(index), out.ctypes.data, out.size,
+                                        ctypes.byref(count)), "moa_fft_plan_table")
+        return out
 
     def destroy(self) -> None:
         if getattr(self, "_h", None):

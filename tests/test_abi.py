@@ -98,6 +98,7 @@ def test_dead_handles_and_null(L):
     assert L.moa_fft_exec_adjoint(bogus, None, None, None) == 1
     assert L.moa_fft_status(bogus) == 1
     assert L.moa_fft_plan_info(bogus, None, None, None, None) == 1
+    assert L.moa_fft_plan_table(bogus, 0, 12, None, 0, None) == 1
     assert L.moa_fft_exec_host(bogus, None, None, None, None) == 1
     assert L.moa_fft_exec_pass(bogus, 0, -1, None, None, None) == 1
     assert L.moa_fft_pass_info(bogus, 0, None, 0, None) == 1
