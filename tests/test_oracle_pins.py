@@ -236,3 +236,36 @@ def test_psi_worked_example(oracle):
         assert list(got) == vals, (kind, idx)
     # the gamma recurrence on the full index <2 1 3>
     assert oracle.gamma(shape, [2, 1, 3]) == 47
+
+
+# -- the gradient of the differentiation workload (closed form) -------------
+
+def test_gradient_closed_form_matches_central_differences(oracle):
+    """L(x) = sum |H * F x|^2 has the gradient dL/dRe + i dL/dIm =
+    2 F^H (|H|^2 * F x), F^H being the sign +1 transform.  L is quadratic, so
+    FP64 central differences are exact up to rounding: at n = 2^8 they pin the
+    closed form that the GPU gradient tests use."""
+    from paper_0811_2535_gb300 import inputs
+    n = 1 << 8
+    H, x = inputs.spectral_filter(n, 1, inputs.SEED_GRADIENT)
+    H = H.astype(np.complex128)
+    x = x.reshape(n).astype(np.complex128)
+
+    def loss(v):
+        return float(np.sum(np.abs(H * oracle.fft_radix2(v, -1)) ** 2))
+
+    h = 1e-3
+    fd = np.empty(n, np.complex128)
+    for j in range(n):
+        parts = []
+        for unit in (1.0, 1j):
+            xp, xm = x.copy(), x.copy()
+            xp[j] += h * unit
+            xm[j] -= h * unit
+            parts.append((loss(xp) - loss(xm)) / (2 * h))
+        fd[j] = parts[0] + 1j * parts[1]
+    closed = 2.0 * oracle.fft_radix2(np.abs(H) ** 2 * oracle.fft_radix2(x, -1), +1)
+    assert rel_l2(closed, fd) < 1e-9
+    # a dropped factor 2 or the forward transform in place of F^H fails
+    assert rel_l2(oracle.fft_radix2(np.abs(H) ** 2 * oracle.fft_radix2(x, -1), +1), fd) > 0.4
+    assert rel_l2(2.0 * oracle.fft_radix2(np.abs(H) ** 2 * oracle.fft_radix2(x, -1), -1), fd) > 0.4
