@@ -188,6 +188,21 @@ def oracle_step(shapes, seed):
     return secs, outs
 
 
+def host_cpu() -> dict:
+    """The host the CPU legs ran on: architecture, CPU model (lscpu), cores."""
+    import platform
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"machine": platform.machine(), "model": model or platform.processor(), "nproc": os.cpu_count()}
+
+
 def template_step(shapes, seed, reps: int = 2):
     """The paper's all-processor templates on every host core: Fig. 6.4 for
     the 1-D transform (m = the largest power of two <= the threads, at most
@@ -273,7 +288,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "sample_scale_log2": scale},
-            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": host_cpu()},
             "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -536,6 +552,7 @@ def run_moa(args):
             "kind": "Fig. 6.4 / Eq. B.6 all-processor templates, OpenMP, FP64",
             "sample": f"one full step, mean of 2 after 1 untimed; 1-D on m = {m} processors",
             "bit_identical_to_oracle": same}
+        cpu_baseline["host"] = host_cpu()
         for (name, shape), o, ref in zip(WORKLOAD, outs, refs):
             y = o.cpu().numpy().astype(np.complex128).reshape(-1)
             r = ref.reshape(-1)

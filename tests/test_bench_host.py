@@ -39,3 +39,9 @@ def test_template_step_small_workload_equals_oracle():
     secs, threads, m, same = bench.template_step([(1 << 12,), (64, 32), (16, 8, 4)], 1, reps=1)
     assert same and secs > 0 and threads >= 1
     assert m >= 1 and (m & (m - 1)) == 0 and m <= threads and m * m <= 1 << 12
+
+
+def test_host_cpu_record():
+    import bench
+    h = bench.host_cpu()
+    assert set(h) == {"machine", "model", "nproc"} and h["nproc"] >= 1 and h["machine"]
