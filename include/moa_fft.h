@@ -169,6 +169,32 @@ MOA_API moa_status_t moa_fft_plan_info(moa_fft_plan_t plan, int *passes, int64_t
 MOA_API moa_status_t moa_fft_pass_info(moa_fft_plan_t plan, int index, char *name, size_t name_len,
                                        int64_t *bytes);
 
+/* Host-only description of the work queue moa_fft_plan_batched builds for
+ * `lengths` (default split, autotuner off; MOA_BATCH_LOG2R applies), without
+ * a GPU.  The persistent blocks of the batched launch take the tasks in
+ * this order (Sec. 4.3: many problems sharing the processors).
+ *   lengths, count : as for moa_fft_plan_batched (same checks and codes).
+ *   resident : blocks that run at once (the plan uses SMs x blocks per SM,
+ *              3 x 152 on GB300); a transform's row tiles are queued about
+ *              this many column tiles after its last column tile.
+ *   order    : NULL or `count` entries; order[k] = index in `lengths` of the
+ *              k-th transform in the plan's grouping (longest first, then
+ *              input order).
+ *   tasks    : 6 int32 per task, in queue order: {first, count, tile,
+ *              log2 n, log2 r, kind}.  kind 0: `count` transforms of 2^log2n
+ *              <= 4096 points at grouping positions first .. first+count-1,
+ *              each in one block; kind 1 / 2: column / row tile `tile` of the
+ *              lifted transform at position `first` (2^log2n = r*c points,
+ *              r = 2^log2r, 2^(log2n - 12) tiles of each kind).  A row tile
+ *              waits for all column tiles of its transform; column tiles never
+ *              wait.  NULL with capacity 0 only reports *ntasks.
+ *   capacity : tasks room, in tasks; ntasks receives the queue length.
+ * MOA_ERR_INVALID_ARG for resident < 1, capacity below the length or a NULL
+ * tasks buffer with capacity > 0. */
+MOA_API moa_status_t moa_fft_batched_queue(const int64_t *lengths, int64_t count, int64_t resident,
+                                           int64_t *order, int32_t *tasks, int64_t capacity,
+                                           int64_t *ntasks);
+
 /* Copy one of the plan's twiddle tables to host memory, for tests and
  * diagnostics: each entry is w_M^e = exp(-2 pi i e / M) evaluated once in
  * FP64 on the device (exact reduction e mod M, Fig. 3.8: weights computed

@@ -533,7 +533,19 @@ int batched_logr(int logn, int dlr)
     return lr;
 }
 
-moa_status_t build_batched(moa_fft_plan_s *p, const int64_t *lengths, int64_t count)
+// The host part of a batched plan: the transforms grouped by length, longest
+// first (offs_sorted: their offsets in that order), and the work queue of
+// small tasks and large-transform tiles.  `resident` is the number of
+// persistent blocks that run at once (SMs x blocks per SM).
+struct BatchQueue {
+    std::vector<int64_t> offs_sorted;
+    std::vector<moa::BatchTask> queue;
+    bool need_stage[13] = {false};
+    bool need_lift[17] = {false};
+    bool has_large = false;
+};
+
+void build_queue(const int64_t *lengths, int64_t count, int dlr, int64_t resident, BatchQueue &bq)
 {
     std::vector<int64_t> offset(count);
     int64_t total = 0;
@@ -541,20 +553,15 @@ moa_status_t build_batched(moa_fft_plan_s *p, const int64_t *lengths, int64_t co
         offset[i] = total;
         total += lengths[i];
     }
-    p->total = total;
-    p->batch = 1;
-    p->dims = 1;
-    p->batched = true;
-
+    std::vector<int64_t> &offs_sorted = bq.offs_sorted;
+    bool *need_stage = bq.need_stage;
+    bool *need_lift = bq.need_lift;
     // group by length, longest first
-    std::vector<int64_t> offs_sorted;
     offs_sorted.reserve(count);
     std::vector<moa::BatchTask> small;
     std::vector<double> small_cost;
     std::vector<int> large;   // positions in offs_sorted of the large transforms, longest first
     std::vector<int8_t> large_logn;
-    bool need_stage[13] = {false};
-    bool need_lift[17] = {false};
     for (int logn = 16; logn >= 1; --logn) {
         std::vector<int64_t> group;
         for (int64_t i = 0; i < count; ++i)
@@ -565,7 +572,7 @@ moa_status_t build_batched(moa_fft_plan_s *p, const int64_t *lengths, int64_t co
         const int first = (int)offs_sorted.size();
         offs_sorted.insert(offs_sorted.end(), group.begin(), group.end());
         if (logn >= 13) {
-            const int lr = batched_logr(logn, p->opt_batch_dlr);
+            const int lr = batched_logr(logn, dlr);
             need_stage[lr] = need_stage[logn - lr] = true;
             need_lift[logn] = true;
             for (size_t k = 0; k < group.size(); ++k) {
@@ -582,17 +589,11 @@ moa_status_t build_batched(moa_fft_plan_s *p, const int64_t *lengths, int64_t co
             }
         }
     }
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return MOA_ERR_CUDA;
-    const int64_t resident = (int64_t)sms * moa::batched_blocks_per_sm();
-
     // Queue: the column tiles of the large transforms in order; each
     // transform's row tiles follow its last column tile about one wave of
     // blocks later (so its workspace is still in L2 when read back and the
     // row tiles rarely wait); then the small tasks, longest first.
-    std::vector<moa::BatchTask> queue;
+    std::vector<moa::BatchTask> &queue = bq.queue;
     {
         struct Pending {
             size_t idx;
@@ -602,12 +603,12 @@ moa_status_t build_batched(moa_fft_plan_s *p, const int64_t *lengths, int64_t co
         size_t next_pending = 0;
         int64_t emitted_cols = 0;
         auto emit_rows = [&](size_t li) {
-            const int logn = large_logn[li], lr = batched_logr(logn, p->opt_batch_dlr);
+            const int logn = large_logn[li], lr = batched_logr(logn, dlr);
             for (int g = 0; g < (1 << (logn - 12)); ++g)
                 queue.push_back(moa::BatchTask{large[li], 1, (int16_t)g, (int8_t)logn, (int8_t)lr, 2, 0});
         };
         for (size_t li = 0; li < large.size(); ++li) {
-            const int logn = large_logn[li], lr = batched_logr(logn, p->opt_batch_dlr);
+            const int logn = large_logn[li], lr = batched_logr(logn, dlr);
             for (int g = 0; g < (1 << (logn - 12)); ++g) {
                 queue.push_back(moa::BatchTask{large[li], 1, (int16_t)g, (int8_t)logn, (int8_t)lr, 1, 0});
                 ++emitted_cols;
@@ -626,6 +627,32 @@ moa_status_t build_batched(moa_fft_plan_s *p, const int64_t *lengths, int64_t co
         for (size_t i : order)
             queue.push_back(small[i]);
     }
+
+    bq.has_large = !large.empty();
+}
+
+moa_status_t build_batched(moa_fft_plan_s *p, const int64_t *lengths, int64_t count)
+{
+    int64_t total = 0;
+    for (int64_t i = 0; i < count; ++i)
+        total += lengths[i];
+    p->total = total;
+    p->batch = 1;
+    p->dims = 1;
+    p->batched = true;
+
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return MOA_ERR_CUDA;
+    const int64_t resident = (int64_t)sms * moa::batched_blocks_per_sm();
+
+    BatchQueue bq;
+    build_queue(lengths, count, p->opt_batch_dlr, resident, bq);
+    const std::vector<int64_t> &offs_sorted = bq.offs_sorted;
+    const std::vector<moa::BatchTask> &queue = bq.queue;
+    const bool *need_stage = bq.need_stage;
+    const bool *need_lift = bq.need_lift;
 
     // device block: status | tasks | offsets | ticket | tables struct | stage tables | two-level tables
     auto align = [](size_t v) { return (v + 255) & ~size_t(255); };
@@ -656,7 +683,7 @@ moa_status_t build_batched(moa_fft_plan_s *p, const int64_t *lengths, int64_t co
     if (dev_alloc(&blk, bytes) != cudaSuccess)
         return MOA_ERR_ALLOC;
     p->batch_block = blk;
-    if (!large.empty()) {
+    if (bq.has_large) {
         void *ws = nullptr;
         p->workspace_bytes = (size_t)total * sizeof(float2);
         if (dev_alloc(&ws, p->workspace_bytes) != cudaSuccess)
@@ -1326,6 +1353,54 @@ moa_status_t moa_fft_pass_info(moa_fft_plan_t plan, int index, char *name, size_
     }
     if (bytes)
         *bytes = 2 * (int64_t)sizeof(float2) * plan->total;
+    return MOA_OK;
+}
+
+moa_status_t moa_fft_batched_queue(const int64_t *lengths, int64_t count, int64_t resident, int64_t *order,
+                                   int32_t *tasks, int64_t capacity, int64_t *ntasks)
+{
+    if (!lengths || count < 1 || resident < 1 || capacity < 0 || (capacity > 0 && !tasks))
+        return MOA_ERR_INVALID_ARG;
+    int64_t total = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        if (!pow2_ge2(lengths[i]))
+            return MOA_ERR_INVALID_SIZE;
+        if (lengths[i] > 65536)
+            return MOA_ERR_UNSUPPORTED;
+        total += lengths[i];
+        if (total >= (int64_t(1) << 31))
+            return MOA_ERR_UNSUPPORTED;
+    }
+    BatchQueue bq;
+    build_queue(lengths, count, 0, resident, bq);
+    const int64_t nt = (int64_t)bq.queue.size();
+    if (ntasks)
+        *ntasks = nt;
+    if (order) {
+        // offsets grow with the input index, so each sorted offset maps back by search
+        std::vector<int64_t> offset(count);
+        int64_t o = 0;
+        for (int64_t i = 0; i < count; ++i) {
+            offset[i] = o;
+            o += lengths[i];
+        }
+        for (int64_t k = 0; k < count; ++k)
+            order[k] = std::lower_bound(offset.begin(), offset.end(), bq.offs_sorted[k]) - offset.begin();
+    }
+    if (capacity == 0)
+        return MOA_OK;
+    if (capacity < nt)
+        return MOA_ERR_INVALID_ARG;
+    for (int64_t t = 0; t < nt; ++t) {
+        const moa::BatchTask &q = bq.queue[t];
+        int32_t *d = tasks + 6 * t;
+        d[0] = q.first;
+        d[1] = q.count;
+        d[2] = q.tile;
+        d[3] = q.logn;
+        d[4] = q.logr;
+        d[5] = q.kind;
+    }
     return MOA_OK;
 }
 

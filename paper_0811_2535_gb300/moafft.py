@@ -45,6 +45,8 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                         ctypes.POINTER(ctypes.c_size_t), ctypes.c_char_p, ctypes.c_size_t]),
     "moa_fft_plan_table": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _I64, ctypes.POINTER(_I64)]),
+    "moa_fft_batched_queue": (ctypes.c_int, [ctypes.POINTER(_I64), _I64, _I64, ctypes.POINTER(_I64),
+                                             ctypes.POINTER(ctypes.c_int32), _I64, ctypes.POINTER(_I64)]),
     "moa_fft_destroy": (ctypes.c_int, [_P]),
 }
 
@@ -85,6 +87,24 @@ def estimate(shape: Sequence[int], batch: int = 1, dtype: int = MOA_C64, tma: in
            "moa_fft_estimate")
     return {"passes": np_.value, "split_r": r.value, "split_c": c.value, "workspace_bytes": ws.value,
             "kernels": buf.value.decode().split(";") if buf.value else []}
+
+
+def batched_queue(lengths: Sequence[int], resident: int):
+    """Host-only work queue of a batched plan (``moa_fft_batched_queue``):
+    returns (order, tasks) with tasks an (ntasks, 6) int32 array of rows
+    {first, count, tile, log2 n, log2 r, kind}.  Needs no GPU."""
+    import numpy as np
+    arr = (_I64 * len(lengths))(*[int(v) for v in lengths])
+    nt = _I64()
+    _check(lib().moa_fft_batched_queue(arr, len(lengths), int(resident), None, None, 0, ctypes.byref(nt)),
+           "moa_fft_batched_queue")
+    order = np.empty(len(lengths), dtype=np.int64)
+    tasks = np.empty((nt.value, 6), dtype=np.int32)
+    _check(lib().moa_fft_batched_queue(arr, len(lengths), int(resident),
+                                       order.ctypes.data_as(ctypes.POINTER(_I64)),
+                                       tasks.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), nt.value,
+                                       ctypes.byref(nt)), "moa_fft_batched_queue")
+    return order, tasks
 
 
 def error_string(code: int) -> str:
