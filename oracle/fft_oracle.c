@@ -102,7 +102,7 @@ int oracle_dft_naive(const double *x, double *y, int64_t n, int sign)
 }
 
 /* ---------------------------------------------------------------------- */
-/* Fig. 2.1, Line 1: x <- P_n x, the bit-reversal permutation.  Element j
+/* Fig. 2.1 begins with x <- P_n x, the bit-reversal permutation.  Element j
  * moves to position bitrev_t(j); the permutation is an involution, so each
  * pair is swapped once. */
 static void bit_reverse_permute(double *x, int64_t n, int t)
@@ -179,7 +179,7 @@ int oracle_fft_radix2_batch(double *x, int64_t n, int64_t batch, int sign)
 /* Sec. 4, Fig. 4.9: the combined plan using partitioned data.
  *
  * m "processors" (a power of two), psize = n/m elements each.  After the
- * bit reversal of Fig. 2.1 Line 1, stages q < breakpoint run in the block
+ * bit reversal that begins Fig. 2.1, stages q < breakpoint run in the block
  * phase: processor p copies the psize consecutive elements starting at
  * p*psize into a private vector xblock, runs those stages on it (each column
  * of length L = 2^q <= psize lies inside the block) and copies it back.

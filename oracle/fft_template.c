@@ -136,7 +136,7 @@ int tmpl_fft_partitioned(double *x, int64_t n, int64_t m, int breakpoint, int si
         return -1;
     int failed = 0;
 
-    /* Fig. 2.1, Line 1: P_n x.  Each pair (j, bitrev(j)) is swapped by the
+    /* Fig. 2.1 begins with P_n x.  Each pair (j, bitrev(j)) is swapped by the
      * iteration with the smaller index only, so the iterations are disjoint. */
 #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) {

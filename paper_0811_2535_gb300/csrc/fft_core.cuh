@@ -10,7 +10,7 @@
 // N/R_1, Sec. 4.2) and each exchange playing the role of the block-to-cyclic
 // redistribution (Sec. 4.6, Fig. 4.9).  The stages form a self-sorting
 // (Stockham) sequence, so input and output are in natural order and no bit
-// reversal (Fig. 2.1 Line 1) is ever materialised.
+// reversal (the first step of Fig. 2.1) is ever materialised.
 //
 // Stage s (K = R_1..R_{s-1} product, M = N/K, M1 = M/R_s):
 //   butterfly b = kappa*M1 + u, kappa < K, u < M1,
