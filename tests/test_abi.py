@@ -126,3 +126,19 @@ def test_allocation_fault_injection():
     assert out.returncode == 0, out.stderr
     rc, hv = out.stdout.split()
     assert int(rc) == 4 and hv == "None"    # MOA_ERR_ALLOC, *plan = NULL
+
+
+def test_header_enums_match_the_binding(L):
+    """The status and dtype values the header declares are the ones the
+    binding uses, and every status code has its own description."""
+    from paper_0811_2535_gb300 import moafft
+    text = open(os.path.join(ROOT, "include", "moa_fft.h")).read()
+    declared = {name: int(val) for name, val in re.findall(r"\b(MOA_(?:OK|ERR_\w+|C64\w*))\s*=\s*(\d+)", text)}
+    status = {v: k for k, v in declared.items() if k == "MOA_OK" or k.startswith("MOA_ERR_")}
+    assert status == moafft.STATUS
+    assert (declared["MOA_C64"], declared["MOA_C64_TC_FP16"], declared["MOA_C64_TC_BF16"]) == \
+        (moafft.MOA_C64, moafft.MOA_C64_TC_FP16, moafft.MOA_C64_TC_BF16)
+    assert (moafft.MOA_OK, moafft.MOA_ERR_TIMEOUT) == (declared["MOA_OK"], declared["MOA_ERR_TIMEOUT"])
+    strings = [L.moa_fft_error_string(code).decode() for code in sorted(status)]
+    assert len(set(strings)) == len(strings) and all(strings)
+    assert L.moa_fft_error_string(99).decode() not in strings[1:]
