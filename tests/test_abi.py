@@ -142,3 +142,18 @@ def test_header_enums_match_the_binding(L):
     strings = [L.moa_fft_error_string(code).decode() for code in sorted(status)]
     assert len(set(strings)) == len(strings) and all(strings)
     assert L.moa_fft_error_string(99).decode() not in strings[1:]
+
+
+def test_binding_signatures_match_header_prototypes():
+    """Every prototype in include/*.h takes as many arguments as the
+    binding's ctypes signature passes, and returns a pointer exactly where
+    the binding expects one (the error-string call)."""
+    from paper_0811_2535_gb300 import moafft
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for ret, name, params in re.findall(r"MOA_API\s+([\w\s\*]+?)\s*\b(moa_\w+)\s*\(([^)]*)\)", text):
+            params = params.strip()
+            n = 0 if params in ("", "void") else params.count(",") + 1
+            res, args = moafft.SIGNATURES[name]
+            assert len(args) == n, (name, n, len(args))
+            assert ("*" in ret) == (res is ctypes.c_char_p), (name, ret)
