@@ -144,8 +144,22 @@ MOA_API moa_status_t moa_fft_exec_host(moa_fft_plan_t plan, const void *host_in,
  * exits.  The first call on a device sets them up (symbol lookup, twiddle
  * generation) and synchronises `stream` once: make that first call before
  * any stream capture.  All calls on a device share the arrays; calls that
- * overlap on the GPU race and must be serialised by the caller. */
+ * overlap on the GPU race and must be serialised by the caller.  A kernel
+ * whose bounded wait gives up records MOA_ERR_TIMEOUT in the device's status
+ * word (the output is then incomplete); read it with
+ * moa_fft_noalloc_status.  Each call looks up the scratch array's address
+ * again (a host-side lookup) and repeats the set-up if the device's context
+ * was made again since (cudaDeviceReset). */
 MOA_API moa_status_t moa_fft_exec_noalloc(const void *in, void *out, int64_t n, int sign, void *stream);
+
+/* Status word of moa_fft_exec_noalloc on the current device: MOA_OK, or the
+ * first error a kernel recorded since the word was last read (for instance
+ * MOA_ERR_TIMEOUT).  The paper has no counterpart.  The word is copied to
+ * the host after the work already queued on `stream` (cudaStream_t or
+ * NULL), then reset to MOA_OK; the call synchronises `stream` and allocates
+ * nothing.  MOA_ERR_CUDA if the copy fails.  Before any transform on the
+ * device it runs the same one-time set-up as moa_fft_exec_noalloc. */
+MOA_API moa_status_t moa_fft_noalloc_status(void *stream);
 
 /* Device status word of the plan (MOA_OK or the first error a kernel
  * recorded), read with a synchronous copy; the word is then reset to

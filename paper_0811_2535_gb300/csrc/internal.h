@@ -22,9 +22,17 @@ enum PassFlags {
     FLAG_CONJ_IN = 1,    // conjugate on load (sign +1 via conj(F_-(conj x)))
     FLAG_CONJ_OUT = 2,   // conjugate on store
     FLAG_TW4 = 4,        // multiply column outputs by w_{N*C}^(k*i) (four-step twiddle)
-    FLAG_PDL = 8         // launch as a programmatic dependent launch of the previous kernel in the
+    FLAG_PDL = 8,        // launch as a programmatic dependent launch of the previous kernel in the
                          // stream (the row, column and pipelined pass kernels wait for it on the device)
+    FLAG_SHORT_WAIT = 16 // fault injection for tests: the pipelined kernels give up on a tile load
+                         // that has not landed at its first test (MOA_ERR_TIMEOUT, no GPU fault)
 };
+
+// Transforms per tile that a plan gives a column pass of 2^logN points over
+// C columns, and a row pass over O rows (transposed: its store is the
+// four-step transpose); the allocation-free entry point uses the same.
+int pick_logF_col(int logN, int64_t C);
+int pick_logF_row(int logN, int64_t O, bool transposed);
 
 // One kernel launch: N-point transforms (N = 2^logN <= 4096) along one axis.
 //  PASS_COL: view [O][N][C] (row-major), transform along the middle axis,

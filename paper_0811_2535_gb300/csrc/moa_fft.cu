@@ -62,6 +62,7 @@ struct moa_fft_plan_s {
     int opt_pipe = -1;            // 0: generic kernels only, 1: pipelined strided kernels allowed
     int opt_batch_dlr = 0;        // batched: log2 r offset from floor(log2 n / 2)
     int opt_lift3 = -1;           // 1-D: 1 = three-level lift (r = 256, fused second/third pass)
+    bool fault_wait = false;      // MOA_FAULT_WAIT=1 at plan time (tests): short device waits
     bool tma = false;             // tensor-map encoder present: pipelined kernels and the two-pass 3-D plan allowed
     moa::Lift3Launch l3{};
     void *l3_block = nullptr;     // two-level table of w_c, task queue, ticket and unit counters
@@ -113,7 +114,9 @@ int tile_log2()
 
 int threads_log2_per_transform(int logN) { return logN < 4 ? 0 : logN - 4; }
 
-int pick_logF_col(int logN, int64_t C)
+}  // namespace
+
+int moa::pick_logF_col(int logN, int64_t C)
 {
     int lf = tile_log2() - logN;
     if (lf < 2)
@@ -129,7 +132,7 @@ int pick_logF_col(int logN, int64_t C)
     return lf < 0 ? 0 : lf;
 }
 
-int pick_logF_row(int logN, int64_t O, bool transposed)
+int moa::pick_logF_row(int logN, int64_t O, bool transposed)
 {
     int lf = tile_log2() - logN;
     if (transposed && lf < 2)
@@ -147,6 +150,8 @@ int pick_logF_row(int logN, int64_t O, bool transposed)
     return lf < 0 ? 0 : lf;
 }
 
+namespace {
+
 PassDesc row_pass(int logN, int64_t O, int64_t Rt, int src, int dst)
 {
     PassDesc d{};
@@ -155,7 +160,7 @@ PassDesc row_pass(int logN, int64_t O, int64_t Rt, int src, int dst)
     d.O = O;
     d.C = 1;
     d.Rt = Rt;
-    d.logF = pick_logF_row(logN, O, Rt > 1);
+    d.logF = moa::pick_logF_row(logN, O, Rt > 1);
     d.src = src;
     d.dst = dst;
     d.tw4 = 0;
@@ -170,7 +175,7 @@ PassDesc col_pass(int logN, int64_t O, int64_t C, int tw4, int src, int dst)
     d.O = O;
     d.C = C;
     d.Rt = 1;
-    d.logF = pick_logF_col(logN, C);
+    d.logF = moa::pick_logF_col(logN, C);
     d.src = src;
     d.dst = dst;
     d.tw4 = tw4;
@@ -775,6 +780,10 @@ moa_status_t run_pass(moa_fft_plan_s *p, size_t i, const void *in, void *out, cu
     // ran slower when its blocks were placed early behind a pipelined kernel.
     if (env_int("MOA_PDL", 1) && (i > 0 || d.pipe))
         flags |= moa::FLAG_PDL;
+    // fault injection (MOA_FAULT_WAIT=1 at plan time): the pipelined kernels
+    // give up on a tile load that has not landed at its first test
+    if (p->fault_wait)
+        flags |= moa::FLAG_SHORT_WAIT;
     if (d.kind == moa::PASS_LIFT3)   // reads the workspace through the tensor map made at plan time
         return moa::launch_lift3(p->l3, buf(d.dst), p->tw.stage[d.logF], p->tw.stage[d.logN], flags, s,
                                  p->d_status) == cudaSuccess
@@ -1026,6 +1035,7 @@ moa_status_t make_plan(moa_fft_plan_s **out, const int64_t *n, int dims, int64_t
     p->opt_pipe = opt_pipe;
     p->opt_lift3 = opt_lift3;
     p->tma = moa::pipe_supported();
+    p->fault_wait = env_int("MOA_FAULT_WAIT", 0) == 1;
     moa_status_t st = build_passes(p);
     if (st == MOA_OK) {
         assign_pipe(p);

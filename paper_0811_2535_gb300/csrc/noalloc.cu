@@ -17,12 +17,23 @@
 // that first call before any stream capture.
 //
 // All calls on one device share the arrays, which keep the last call's
-// contents (nothing in them needs to start at zero except the status word,
-// which every call clears).  Calls on one device that overlap on the GPU,
-// for instance on two streams, race on the scratch and the status word;
-// calls on different devices do not interact.
+// contents (nothing in them needs to start at zero except the status word).
+// Calls on one device that overlap on the GPU, for instance on two streams,
+// race on the scratch and the status word; calls on different devices do not
+// interact.
+//
+// The status word collects what the kernels' bounded waits report
+// (MOA_ERR_TIMEOUT); moa_fft_noalloc_status reads it after the caller's work
+// on a stream and clears it.  A call does not clear it, so an error stays
+// until it is read.
+//
+// If the device's context is destroyed and made again (cudaDeviceReset),
+// the module is loaded afresh: the arrays get new addresses and lose their
+// tables.  Every call therefore looks the scratch array's address up again
+// (a host-side lookup) and repeats the set-up when it has moved.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <mutex>
 
 #include "fft_core.cuh"
@@ -110,20 +121,24 @@ moa_status_t setup(int dev, cudaStream_t stream, DeviceState &st)
     return MOA_OK;
 }
 
-// Transforms per tile, as the plan would choose them (4096-point tiles, at
-// least four transforms when the tile is strided or transposed).
-int logF_for(int logN, int64_t count, bool strided)
+// The device's arrays, set up for the current context: the scratch array's
+// address is looked up again and compared with the one the set-up recorded.
+moa_status_t ready_state(int dev, cudaStream_t s, DeviceState &out)
 {
-    int lf = 12 - logN;
-    if (strided && lf < 2)
-        lf = 2;
-    const int cap = strided ? moa::max_logF_interleaved(logN) : 10 - (logN < 4 ? 0 : logN - 4);
-    if (lf > cap)
-        lf = cap;
-    const int lc = ilog2(count);
-    if (lf > lc)
-        lf = lc;
-    return lf < 0 ? 0 : lf;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess)
+        return MOA_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState &st = g_dev[dev];
+    if (st.ready && st.scratch != static_cast<float2 *>(p))
+        st.ready = false;   // the context was made again: the arrays moved
+    if (!st.ready) {
+        const moa_status_t rc = setup(dev, s, st);
+        if (rc != MOA_OK)
+            return rc;
+    }
+    out = st;
+    return MOA_OK;
 }
 
 }  // namespace
@@ -143,24 +158,21 @@ extern "C" moa_status_t moa_fft_exec_noalloc(const void *in, void *out, int64_t 
         return MOA_ERR_CUDA;
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
     DeviceState st;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_dev[dev].ready) {
-            const moa_status_t rc = setup(dev, s, g_dev[dev]);
-            if (rc != MOA_OK)
-                return rc;
-        }
-        st = g_dev[dev];
-    }
-    if (cudaMemsetAsync(st.status, 0, sizeof(int), s) != cudaSuccess)
-        return MOA_ERR_CUDA;
+    const moa_status_t rc = ready_state(dev, s, st);
+    if (rc != MOA_OK)
+        return rc;
 
     moa::TwiddleSet tw{};
     for (int l = 1; l <= 12; ++l)
         tw.stage[l] = moa::stage_table_entries(l) > 0 ? st.stage + st.stage_off[l] : nullptr;
     const int L = ilog2(n);
-    const int first = sign > 0 ? moa::FLAG_CONJ_IN : 0;
-    const int last = sign > 0 ? moa::FLAG_CONJ_OUT : 0;
+    // fault injection for tests (MOA_FAULT_WAIT=1 at call time): the
+    // pipelined kernels give up on a tile load that has not landed at its
+    // first test
+    const char *fw = std::getenv("MOA_FAULT_WAIT");
+    const int fault = (fw && std::atoi(fw) == 1) ? moa::FLAG_SHORT_WAIT : 0;
+    const int first = (sign > 0 ? moa::FLAG_CONJ_IN : 0) | fault;
+    const int last = (sign > 0 ? moa::FLAG_CONJ_OUT : 0) | fault;
     const bool pipe_ok = moa::pipe_supported();
     const float2 *src = static_cast<const float2 *>(in);
     float2 *dst = static_cast<float2 *>(out);
@@ -171,7 +183,7 @@ extern "C" moa_status_t moa_fft_exec_noalloc(const void *in, void *out, int64_t 
         d.O = 1;
         d.C = 1;
         d.Rt = 1;
-        d.logF = 0;
+        d.logF = moa::pick_logF_row(L, 1, false);
         return moa::launch_pass(d, src, dst, tw, first | last, s, st.status) == cudaSuccess ? MOA_OK
                                                                                             : MOA_ERR_CUDA;
     }
@@ -188,7 +200,7 @@ extern "C" moa_status_t moa_fft_exec_noalloc(const void *in, void *out, int64_t 
     p1.O = 1;
     p1.C = c;
     p1.Rt = 1;
-    p1.logF = logF_for(lr, c, true);
+    p1.logF = moa::pick_logF_col(lr, c);
     p1.tw4 = 1;
     p1.pipe = pipe_ok && lr >= 10 && p1.logF == 2 && c >= 4;
     moa::PassDesc p2{};
@@ -197,11 +209,28 @@ extern "C" moa_status_t moa_fft_exec_noalloc(const void *in, void *out, int64_t 
     p2.O = r;
     p2.C = 1;
     p2.Rt = r;
-    p2.logF = logF_for(lc, r, true);
+    p2.logF = moa::pick_logF_row(lc, r, true);
     p2.pipe = pipe_ok && lc >= 10 && p2.logF == 2;
     if (moa::launch_pass(p1, src, st.scratch, tw, first, s, st.status) != cudaSuccess)
         return MOA_ERR_CUDA;
     if (moa::launch_pass(p2, st.scratch, dst, tw, last, s, st.status) != cudaSuccess)
         return MOA_ERR_CUDA;
     return MOA_OK;
+}
+
+extern "C" moa_status_t moa_fft_noalloc_status(void *stream)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return MOA_ERR_CUDA;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DeviceState st;
+    const moa_status_t rc = ready_state(dev, s, st);
+    if (rc != MOA_OK)
+        return rc;
+    int word = 0;
+    if (cudaMemcpyAsync(&word, st.status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemsetAsync(st.status, 0, sizeof(int), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        return MOA_ERR_CUDA;
+    return static_cast<moa_status_t>(word);
 }

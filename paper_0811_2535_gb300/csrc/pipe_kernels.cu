@@ -121,10 +121,32 @@ struct PipeSmem {
     }
 };
 
-// Bounded wait on an mbarrier phase by one thread; on timeout the status word
-// gets MOA_ERR_TIMEOUT and *abort_flag is set.
-__device__ __forceinline__ void bounded_wait(uint64_t *bar, uint32_t parity, int *status, int *abort_flag)
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity)
 {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase by one thread; on timeout the status word
+// gets MOA_ERR_TIMEOUT and *abort_flag is set.  With FLAG_SHORT_WAIT (fault
+// injection for tests) the wait is a single test, which gives up on a load
+// still in flight.
+__device__ __forceinline__ void bounded_wait(uint64_t *bar, uint32_t parity, int *status, int *abort_flag, int flags)
+{
+    if (flags & FLAG_SHORT_WAIT) {
+        if (!mbar_test_wait(bar, parity)) {
+            atomicExch(status, 6);   // MOA_ERR_TIMEOUT
+            *abort_flag = 1;
+        }
+        return;
+    }
     uint32_t polls = 0;
     while (!mbar_try_wait(bar, parity)) {
         if (++polls >= kMaxPolls) {
@@ -133,6 +155,15 @@ __device__ __forceinline__ void bounded_wait(uint64_t *bar, uint32_t parity, int
             return;
         }
     }
+}
+
+// After a wait gave up: wait (bounded) for the tile's loads still in flight,
+// so that no copy lands in shared memory the block has given up.
+__device__ __forceinline__ void drain_in_flight(uint64_t *bar, uint32_t parity)
+{
+    for (int b = 0; b < 2; ++b)
+        for (uint32_t polls = 0; polls < kMaxPolls && !mbar_try_wait(&bar[b], parity); ++polls) {
+        }
 }
 
 // The three radix stages of N = 1024, 2048, 4096 (radix 4/8/16, 16, 16) with
@@ -236,8 +267,10 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
         if (next >= ntiles)
             pdl_launch_dependents();   // the block's last tile: let the next kernel launch
         if (tid == 0) {
-            bounded_wait(&bar[0], parity, status, abort_flag);
-            bounded_wait(&bar[1], parity, status, abort_flag);
+            bounded_wait(&bar[0], parity, status, abort_flag, flags);
+            bounded_wait(&bar[1], parity, status, abort_flag, flags);
+            if (*abort_flag)
+                drain_in_flight(bar, parity);
         }
         __syncthreads();
         if (*abort_flag)
@@ -361,8 +394,10 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
         if (next >= ntiles)
             pdl_launch_dependents();   // the block's last tile: let the next kernel launch
         if (tid == 0) {
-            bounded_wait(&bar[0], parity, status, abort_flag);
-            bounded_wait(&bar[1], parity, status, abort_flag);
+            bounded_wait(&bar[0], parity, status, abort_flag, flags);
+            bounded_wait(&bar[1], parity, status, abort_flag, flags);
+            if (*abort_flag)
+                drain_in_flight(bar, parity);
         }
         __syncthreads();
         if (*abort_flag)
@@ -448,7 +483,24 @@ template <int LOGN> size_t col_smem()
 }
 template <int LOGN> size_t rowT_smem() { return PipeSmem::bytes<LOGN>(); }
 
-int g_num_sms = 0;
+// SM count of each device (set by prepare_pipe_kernels for the current
+// device; the persistent grids are sized from the device they launch on).
+constexpr int kMaxDev = 64;
+int g_num_sms[kMaxDev] = {0};
+
+int num_sms_current()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev)
+        return 1;
+    int n = __atomic_load_n(&g_num_sms[dev], __ATOMIC_RELAXED);
+    if (n <= 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            return 1;
+        __atomic_store_n(&g_num_sms[dev], n, __ATOMIC_RELAXED);
+    }
+    return n;
+}
 
 // Column pass over the [O][N][C] view (BLK 0 or 1) or the second pass of the
 // lifted transform over the blocked workspace (BLK 2; O = B, C = r).
@@ -485,7 +537,8 @@ cudaError_t launch_col(const PassDesc &d, int64_t O, int64_t C, int blk, const f
     while ((int64_t(1) << logTpo) < (C >> 2))
         ++logTpo;
     const int ntiles = (int)(O << logTpo);
-    const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
+    const int nsm = num_sms_current();
+    const int grid = ntiles < nsm ? ntiles : nsm;
     const size_t smem = col_smem<LOGN>();
     const int Ci = (int)C;
     auto kern = blk == 2 ? pipe_col_kernel<LOGN, false, 2>
@@ -513,7 +566,8 @@ cudaError_t launch_plane2(int64_t O, const float2 *in, float2 *out, const Twiddl
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     const int ntiles = (int)(O << 10);   // 16 row groups x 64 column groups per array
-    const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
+    const int nsm = num_sms_current();
+    const int grid = ntiles < nsm ? ntiles : nsm;
     return launch_maybe_dependent(pipe_col_kernel<12, false, 3>, grid, 1024, col_smem<12>(), stream, flags & FLAG_PDL,
                                   map, out, 256, 10, ntiles, tw.stage[12], tw.lo, tw.hi, tw.h, flags, status);
 }
@@ -523,7 +577,8 @@ cudaError_t launch_rowT(const PassDesc &d, const float2 *in, float2 *out, const 
                         cudaStream_t stream, int *status)
 {
     const int ntiles = (int)((d.O + 3) / 4);
-    const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
+    const int nsm = num_sms_current();
+    const int grid = ntiles < nsm ? ntiles : nsm;
     return launch_maybe_dependent(pipe_rowT_kernel<LOGN>, grid, 1 << (LOGN - 2), rowT_smem<LOGN>(), stream,
                                   flags & FLAG_PDL, in, out, d.O, d.Rt, ntiles, tw.stage[LOGN], flags, status);
 }
@@ -572,8 +627,11 @@ cudaError_t prepare_pipe_kernels()
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
         return e;
-    if ((e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    int nsm = 0;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
+    if (dev < kMaxDev)
+        __atomic_store_n(&g_num_sms[dev], nsm, __ATOMIC_RELAXED);
     if ((e = set_pipe_attrs<10>()) || (e = set_pipe_attrs<11>()) || (e = set_pipe_attrs<12>()))
         return e;
     if ((e = cudaFuncSetAttribute(pipe_col_kernel<12, false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -36,6 +36,7 @@ SIGNATURES = {
     "moa_fft_exec_pass": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
     "moa_fft_exec_host": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "moa_fft_exec_noalloc": (ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P]),
+    "moa_fft_noalloc_status": (ctypes.c_int, [_P]),
     "moa_fft_status": (ctypes.c_int, [_P]),
     "moa_fft_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "moa_fft_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64),

@@ -424,3 +424,29 @@ def test_largest_plan(env, shape, monkeypatch):
         assert per_transform_rel(yb, ref, 1).max() <= TOL, b
     del x, y
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("shape", [(1 << 20,), (4096, 4096), (256, 256, 256)])
+def test_pipelined_wait_timeout_is_reported_and_contained(env, shape, monkeypatch):
+    """Failure detection without a GPU fault: with MOA_FAULT_WAIT=1 at plan
+    time the pipelined kernels give up on the first tile load that has not
+    landed at its first test, wait for their loads in flight and return.  The
+    plan's status word reads MOA_ERR_TIMEOUT (then clear), and a plan made
+    afterwards on the same context is right."""
+    torch, moafft, _ = env
+    from paper_0811_2535_gb300 import inputs
+    monkeypatch.setenv("MOA_AUTOTUNE", "0")
+    x = inputs.uniform(shape, 4100)
+    xd = torch.from_numpy(x.reshape(-1)).cuda()
+    monkeypatch.setenv("MOA_FAULT_WAIT", "1")
+    plan = moafft.Plan(list(shape), 1, -1)
+    monkeypatch.delenv("MOA_FAULT_WAIT")
+    assert any("pipe_col" in plan.pass_info(i)["kernel"] or "pipe_rowT" in plan.pass_info(i)["kernel"]
+               for i in range(plan.info()["passes"]))
+    plan.exec(xd)
+    torch.cuda.synchronize()
+    assert plan.status() == moafft.MOA_ERR_TIMEOUT
+    assert plan.status() == 0
+    plan.destroy()
+    y, _ = run(env, list(shape), 1, -1, x)
+    assert per_transform_rel(y, oracle_ref(env, x, list(shape), 1, -1), 1).max() <= TOL

@@ -1,24 +1,27 @@
-"""The allocation-free entry point moa_fft_exec_noalloc (GPU).
+"""The allocation-free entry points moa_fft_exec_noalloc and
+moa_fft_noalloc_status (GPU).
 
-It exists for callers that may not allocate device memory (their memory is
+They exist for callers that may not allocate device memory (their memory is
 owned by a custom allocator, or their code path must never enter the CUDA
-allocator); it keeps its scratch and twiddle tables in static device arrays.
-This file is collected last so that a run stopping at the first failure has
-already run every other test; it passes alone in a fresh process too.
+allocator); the transform keeps its scratch and twiddle tables in static
+device arrays.  This file is collected last so that a run stopping at the
+first failure has already run every other test; it passes alone in a fresh
+process too.
 
-Checks, through the C ABI: the output equals the planned transform's
-(moa_fft_exec) within the parity tolerance, on two calls in a row; device
-memory in use does not change across calls after the first; sizes beyond
-the 2^20-point static scratch are rejected."""
-import ctypes
-
+Checks, through the C ABI: the output equals the FP64 oracle's within the
+parity tolerance (rel-L2 <= 2e-6), on two calls in a row, for one-tile,
+lifted and pipelined sizes, both signs, in place too; the status word reads
+MOA_OK after each call; device memory in use does not change across calls
+after the first; a wait that gives up (the short-wait fault injection, no
+GPU fault) is reported through moa_fft_noalloc_status and the next call is
+right again; sizes beyond the 2^20-point static scratch are rejected."""
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
 
 TOL = 2e-6
-MOA_ERR_INVALID_SIZE, MOA_ERR_UNSUPPORTED = 2, 3
+MOA_OK, MOA_ERR_INVALID_ARG, MOA_ERR_INVALID_SIZE, MOA_ERR_UNSUPPORTED, MOA_ERR_TIMEOUT = 0, 1, 2, 3, 6
 
 
 @pytest.fixture(scope="module")
@@ -27,8 +30,10 @@ def env():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_0811_2535_gb300 import build, moafft
+    import oracle
     build.build()
-    return torch, moafft
+    oracle.build()
+    return torch, moafft, oracle
 
 
 def rel(a, b):
@@ -37,56 +42,97 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+def stream_of(torch):
+    return torch.cuda.current_stream().cuda_stream
+
+
 def noalloc(moafft, torch, x, out, sign):
-    stream = torch.cuda.current_stream().cuda_stream
-    return moafft.lib().moa_fft_exec_noalloc(x.data_ptr(), out.data_ptr(), x.numel(), sign, stream)
+    return moafft.lib().moa_fft_exec_noalloc(x.data_ptr(), out.data_ptr(), x.numel(), sign, stream_of(torch))
 
 
-@pytest.mark.parametrize("t", [1, 10, 13, 16, 20])
+def status(moafft, torch):
+    return moafft.lib().moa_fft_noalloc_status(stream_of(torch))
+
+
+@pytest.mark.parametrize("t", [1, 10, 13, 16, 19, 20])
 @pytest.mark.parametrize("sign", [-1, 1])
-def test_noalloc_matches_planned_transform_twice(env, t, sign):
-    torch, moafft = env
+def test_noalloc_matches_oracle_twice(env, t, sign):
+    torch, moafft, oracle = env
     from paper_0811_2535_gb300 import inputs
     n = 1 << t
-    x = torch.from_numpy(inputs.uniform(n, 7000 + t)).cuda()
-    plan = moafft.Plan([n], 1, sign)
-    ref = plan.exec(x).cpu().numpy()
-    plan.destroy()
+    x0 = inputs.uniform(n, 7000 + t)
+    ref = oracle.fft_radix2(x0.astype(np.complex128), sign)
+    x = torch.from_numpy(x0).cuda()
     for _ in range(2):
         out = torch.full_like(x, complex(float("nan"), 0.0))
-        assert noalloc(moafft, torch, x, out, sign) == 0
-        torch.cuda.synchronize()
+        assert noalloc(moafft, torch, x, out, sign) == MOA_OK
+        assert status(moafft, torch) == MOA_OK
         assert rel(out.cpu().numpy(), ref) <= TOL
 
 
-def test_noalloc_in_place_and_memory_steady(env):
-    torch, moafft = env
+@pytest.mark.parametrize("t", [10, 19, 20])
+def test_noalloc_in_place(env, t):
+    """One row pass (2^10), the odd split with a pipelined row pass (2^19 =
+    2^9 x 2^10) and the two pipelined passes (2^20), each with in == out."""
+    torch, moafft, oracle = env
+    from paper_0811_2535_gb300 import inputs
+    n = 1 << t
+    x0 = inputs.uniform(n, 7100 + t)
+    ref = oracle.fft_radix2(x0.astype(np.complex128), -1)
+    y = torch.from_numpy(x0).cuda()
+    assert noalloc(moafft, torch, y, y, -1) == MOA_OK
+    assert status(moafft, torch) == MOA_OK
+    assert rel(y.cpu().numpy(), ref) <= TOL
+
+
+def test_noalloc_memory_steady(env):
+    torch, moafft, _ = env
     from paper_0811_2535_gb300 import inputs
     n = 1 << 20
-    x0 = inputs.uniform(n, 7100)
-    x = torch.from_numpy(x0).cuda()
+    x = torch.from_numpy(inputs.uniform(n, 7200)).cuda()
     out = torch.empty_like(x)
-    assert noalloc(moafft, torch, x, out, -1) == 0          # first call: set-up on this device
+    assert noalloc(moafft, torch, x, out, -1) == MOA_OK      # first call: set-up on this device
     torch.cuda.synchronize()
     free_before, _ = torch.cuda.mem_get_info()
     for _ in range(3):
-        assert noalloc(moafft, torch, x, out, -1) == 0
+        assert noalloc(moafft, torch, x, out, -1) == MOA_OK
+    assert status(moafft, torch) == MOA_OK
     torch.cuda.synchronize()
     free_after, _ = torch.cuda.mem_get_info()
     assert free_after == free_before
-    y = x.clone()
-    assert noalloc(moafft, torch, y, y, -1) == 0            # in place
-    torch.cuda.synchronize()
-    assert rel(y.cpu().numpy(), out.cpu().numpy()) <= TOL
+
+
+def test_noalloc_wait_timeout_is_reported(env, monkeypatch):
+    """Failure detection without a GPU fault: with MOA_FAULT_WAIT=1 at call
+    time the pipelined kernels of a 2^20 transform give up on the first tile
+    load that has not landed at its first test; each block then waits for its
+    loads in flight and returns.  The status word reads MOA_ERR_TIMEOUT once
+    and is then clear, and the next call is right."""
+    torch, moafft, oracle = env
+    from paper_0811_2535_gb300 import inputs
+    n = 1 << 20
+    x0 = inputs.uniform(n, 7300)
+    x = torch.from_numpy(x0).cuda()
+    out = torch.empty_like(x)
+    assert noalloc(moafft, torch, x, out, -1) == MOA_OK      # set-up before the fault knob
+    assert status(moafft, torch) == MOA_OK
+    monkeypatch.setenv("MOA_FAULT_WAIT", "1")
+    assert noalloc(moafft, torch, x, out, -1) == MOA_OK
+    monkeypatch.delenv("MOA_FAULT_WAIT")
+    assert status(moafft, torch) == MOA_ERR_TIMEOUT
+    assert status(moafft, torch) == MOA_OK                   # reading clears it
+    assert noalloc(moafft, torch, x, out, -1) == MOA_OK
+    assert status(moafft, torch) == MOA_OK
+    assert rel(out.cpu().numpy(), oracle.fft_radix2(x0.astype(np.complex128), -1)) <= TOL
 
 
 def test_noalloc_rejects_sizes(env):
-    torch, moafft = env
+    torch, moafft, _ = env
     L = moafft.lib()
     big = torch.empty(1 << 21, dtype=torch.complex64, device="cuda")
-    s = torch.cuda.current_stream().cuda_stream
+    s = stream_of(torch)
     assert L.moa_fft_exec_noalloc(big.data_ptr(), big.data_ptr(), 1 << 21, -1, s) == MOA_ERR_UNSUPPORTED
     assert L.moa_fft_exec_noalloc(big.data_ptr(), big.data_ptr(), 3, -1, s) == MOA_ERR_INVALID_SIZE
     assert L.moa_fft_exec_noalloc(big.data_ptr(), big.data_ptr(), 1, -1, s) == MOA_ERR_INVALID_SIZE
-    assert L.moa_fft_exec_noalloc(None, big.data_ptr(), 1024, -1, s) == 1
-    assert L.moa_fft_exec_noalloc(big.data_ptr(), big.data_ptr(), 1024, 0, s) == 1
+    assert L.moa_fft_exec_noalloc(None, big.data_ptr(), 1024, -1, s) == MOA_ERR_INVALID_ARG
+    assert L.moa_fft_exec_noalloc(big.data_ptr(), big.data_ptr(), 1024, 0, s) == MOA_ERR_INVALID_ARG
