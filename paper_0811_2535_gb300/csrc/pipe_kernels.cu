@@ -24,6 +24,8 @@
 // status word and the whole block returns.
 #include <cuda.h>
 
+#include <cstdlib>
+
 #include "fft_core.cuh"
 #include "internal.h"
 #include "pdl.cuh"
@@ -87,6 +89,34 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
+
+// Asynchronous stores from shared memory (TMA, bulk-group completion).
+__device__ __forceinline__ void bulk_store(void *gdst, const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map), "r"(x),
+                 "r"(y), "r"(smem_u32(src))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, const void *src, int x, int y, int z, int w)
+{
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(map),
+                 "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(src))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the staged data has been read out of shared memory (it may be reused)
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// the stores are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Upper bound on mbarrier polls before a wait is declared failed (each
 // try_wait may suspend the thread for a while; a normal tile load completes
@@ -209,11 +239,24 @@ __device__ __forceinline__ void three_stages(float2 (&v)[16], float2 *E, int tau
 //            DFT (over j1a) takes no twiddle, so the tile computes the 2-D DFT
 //            over (j1a, j0); output k = k1a + 16*k0 goes to
 //            X[k0][k1b + 16*k1a][column].
+//
+// Staged stores (N = 4096, `staged` != 0): once the last exchange has been
+// read, the exchange buffer E has room for the late rows of the next tile
+// (its first 40 KiB) and for twelve of the tile's sixteen output slices
+// (slice k = outputs tau + 256k of the four columns, 8 KiB each).  The
+// threads write those slices to E and one thread hands them to TMA stores
+// (BLK = 1: one bulk copy of the tile's first 96 KiB of blocked output;
+// BLK = 0, 2: a 2-D tensor map over the output rows, one 256-row box per
+// slice; BLK = 3: a 4-D tensor map {columns, k1b, k1a, planes}, one box of
+// 16 x 16 rows per slice); the other four slices go out as plain stores.
+// The TMA engine then drains the outputs while the next tile lands and
+// computes; the slices must have left E before the next tile's first
+// exchange, which one thread waits for at the tile start.
 template <int LOGN, bool TW4, int BLK>
 __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
-    pipe_col_kernel(const __grid_constant__ CUtensorMap tmap, float2 *out, int C, int logTpo, int ntiles,
-                    const float2 *__restrict__ tw, const float2 *__restrict__ tw_lo, const float2 *__restrict__ tw_hi,
-                    int tw_h, int flags, int *status)
+    pipe_col_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap, float2 *out,
+                    int C, int logTpo, int ntiles, const float2 *__restrict__ tw, const float2 *__restrict__ tw_lo,
+                    const float2 *__restrict__ tw_hi, int tw_h, int flags, int staged, int *status)
 {
     using Sc = Sched<LOGN>;
     constexpr int N = Sc::N, T = Sc::T;
@@ -273,8 +316,11 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
                 drain_in_flight(bar, parity);
         }
         __syncthreads();
-        if (*abort_flag)
+        if (*abort_flag) {
+            if (LOGN == 12 && staged && tid == 0)
+                bulk_wait_all();   // no staged store may still read E
             return;
+        }
         parity ^= 1u;
 
         // element tau + T*q lands in register (q % NB0)*R0 + q / NB0 (stage-0 order);
@@ -287,6 +333,8 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
             const float2 *src = q * T < HR ? H + (tau + T * q) * 4 : E + (tau + T * q - HR) * 4;
             v[(q % NB0) * R0 + q / NB0] = src[f];
         }
+        if (LOGN == 12 && staged && tid == 0)
+            bulk_wait_read();   // the previous tile's staged outputs have left E
         __syncthreads();   // H and E have been read
         if (tid == 0 && next < ntiles) {
             fence_proxy_async();
@@ -320,30 +368,70 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
             for (int k = 0; k < 16; ++k)
                 v[k].y = -v[k].y;
         }
-        if constexpr (BLK == 3) {
-            // output k = k1a + 16*k0 with tau + T*k = k: k1a = tau % 16, k0 = tau/16 + 16*k
-            static_assert(N == 4096 && T == 256, "the 3-D second pass is a 16 x 256 tile");
-            float2 *dst = out + ((int64_t)o << 24) + (int64_t)(tau >> 4) * 65536 +
-                          ((col >> 8) + 16 * (tau & 15)) * 256 + (col & 255);
+        // outputs k >= k0 of the thread with plain stores
+        auto store_plain = [&](int k0) {
+            if constexpr (BLK == 3) {
+                // output k = k1a + 16*k0 with tau + T*k = k: k1a = tau % 16, k0 = tau/16 + 16*k
+                static_assert(N == 4096 && T == 256, "the 3-D second pass is a 16 x 256 tile");
+                float2 *dst = out + ((int64_t)o << 24) + (int64_t)(tau >> 4) * 65536 +
+                              ((col >> 8) + 16 * (tau & 15)) * 256 + (col & 255);
 #pragma unroll
-            for (int k = 0; k < 16; ++k)
-                dst[(int64_t)k << 20] = v[k];
-        } else if constexpr (BLK == 1) {
-            // element (tau + T*k, col) of the tile: block ((col/4)*(N/4) + (tau + T*k)/4),
-            // slot f*4 + tau%4 (T is a multiple of 4)
-            float2 *dst = out + (int64_t)o * N * C + (int64_t)((col >> 2) * (N >> 2)) * 16 + f * 4 + (tau >> 2) * 16 +
-                          (tau & 3);
+                for (int k = 0; k < 16; ++k)
+                    if (k >= k0)
+                        dst[(int64_t)k << 20] = v[k];
+            } else if constexpr (BLK == 1) {
+                // element (tau + T*k, col) of the tile: block ((col/4)*(N/4) + (tau + T*k)/4),
+                // slot f*4 + tau%4 (T is a multiple of 4)
+                float2 *dst = out + (int64_t)o * N * C + (int64_t)((col >> 2) * (N >> 2)) * 16 + f * 4 +
+                              (tau >> 2) * 16 + (tau & 3);
 #pragma unroll
-            for (int k = 0; k < 16; ++k)
-                dst[k * 4 * T] = v[k];
+                for (int k = 0; k < 16; ++k)
+                    if (k >= k0)
+                        dst[k * 4 * T] = v[k];
+            } else {
+                float2 *dst = out + (int64_t)o * N * C + col + (int64_t)tau * C;
+                const int64_t step = (int64_t)T * C;
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (k >= k0)
+                        dst[k * step] = v[k];
+            }
+        };
+        if (LOGN == 12 && staged) {
+            // slices 0..KS-1 to E behind the late rows of the next tile, the rest plain
+            constexpr int LATE = N - HR;
+            constexpr int KS = (PipeSmem::E_entries<LOGN>() - 4 * LATE) / (4 * T);
+            static_assert(KS >= 1 && KS < 16 && (4 * LATE * 8) % 1024 == 0, "staging slices");
+            float2 *stg = E + 4 * LATE;
+            const int sidx = BLK == 1 ? (tau >> 2) * 16 + f * 4 + (tau & 3) : tau * 4 + f;
+#pragma unroll
+            for (int k = 0; k < KS; ++k)
+                stg[k * 4 * T + sidx] = v[k];
+            store_plain(KS);
+            __syncthreads();   // the staged slices are complete
+            if (tid == 0) {
+                fence_proxy_async();   // written through the generic proxy, read by TMA
+                const int c0 = (tile & tpo_mask) << 2;
+                if constexpr (BLK == 1) {
+                    bulk_store(out + (int64_t)o * N * C + (int64_t)(c0 >> 2) * (N >> 2) * 16, stg,
+                               (uint32_t)(KS * 4 * T * sizeof(float2)));
+                } else {
+#pragma unroll 1
+                    for (int k = 0; k < KS; ++k) {
+                        if constexpr (BLK == 3)
+                            tma_store_4d(&omap, stg + k * 4 * T, 2 * (c0 & 255), c0 >> 8, 0, o * 256 + 16 * k);
+                        else
+                            tma_store_2d(&omap, stg + k * 4 * T, 2 * c0, o * N + T * k);
+                    }
+                }
+                bulk_commit();
+            }
         } else {
-            float2 *dst = out + (int64_t)o * N * C + col + (int64_t)tau * C;
-            const int64_t step = (int64_t)T * C;
-#pragma unroll
-            for (int k = 0; k < 16; ++k)
-                dst[k * step] = v[k];
+            store_plain(0);
         }
     }
+    if (LOGN == 12 && staged && tid == 0)
+        bulk_wait_all();   // the staged stores are complete before the block exits
 }
 
 // Transposed row pass: rows o = 4*tile + f of the [O][N] view; output
@@ -502,6 +590,33 @@ int num_sms_current()
     return n;
 }
 
+// Staged stores of the N = 4096 column passes (MOA_STAGED=0 turns them off).
+bool staged_enabled()
+{
+    static const bool on = [] {
+        const char *s = std::getenv("MOA_STAGED");
+        return !(s && *s && std::atoi(s) == 0);
+    }();
+    return on;
+}
+
+// Output tensor map of the staged stores over the [O][N][C] view: {2C floats,
+// O*N rows}, boxes of 4 columns x 256 rows.  False when the output cannot be
+// a TMA target (not 16-byte aligned).
+bool encode_out_rows(CUtensorMap *map, float2 *out, int64_t O, int64_t C, int logN)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc || (reinterpret_cast<uintptr_t>(out) & 15) != 0)
+        return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)(2 * C), (cuuint64_t)(O << logN)};
+    const cuuint64_t strides[1] = {(cuuint64_t)(2 * C * sizeof(float))};
+    const cuuint32_t box[2] = {8, 256};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, out, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Column pass over the [O][N][C] view (BLK 0 or 1) or the second pass of the
 // lifted transform over the blocked workspace (BLK 2; O = B, C = r).
 template <int LOGN>
@@ -541,11 +656,17 @@ cudaError_t launch_col(const PassDesc &d, int64_t O, int64_t C, int blk, const f
     const int grid = ntiles < nsm ? ntiles : nsm;
     const size_t smem = col_smem<LOGN>();
     const int Ci = (int)C;
+    // staged stores: blocked output by bulk copy (16-byte aligned output),
+    // row output through a tensor map
+    CUtensorMap omap = map;
+    int staged = 0;
+    if (LOGN == 12 && staged_enabled())
+        staged = blk == 1 ? (reinterpret_cast<uintptr_t>(out) & 15) == 0 : encode_out_rows(&omap, out, O, C, LOGN);
     auto kern = blk == 2 ? pipe_col_kernel<LOGN, false, 2>
                          : (d.tw4 && blk == 1 ? pipe_col_kernel<LOGN, true, 1>
                                               : (d.tw4 ? pipe_col_kernel<LOGN, true, 0> : pipe_col_kernel<LOGN, false, 0>));
-    return launch_maybe_dependent(kern, grid, 1 << (LOGN - 2), smem, stream, flags & FLAG_PDL, map, out, Ci, logTpo,
-                                  ntiles, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags, status);
+    return launch_maybe_dependent(kern, grid, 1 << (LOGN - 2), smem, stream, flags & FLAG_PDL, map, omap, out, Ci,
+                                  logTpo, ntiles, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags, staged, status);
 }
 
 // Second pass of the two-pass 3-D transform of O arrays of 256^3 (BLK = 3).
@@ -568,8 +689,23 @@ cudaError_t launch_plane2(int64_t O, const float2 *in, float2 *out, const Twiddl
     const int ntiles = (int)(O << 10);   // 16 row groups x 64 column groups per array
     const int nsm = num_sms_current();
     const int grid = ntiles < nsm ? ntiles : nsm;
+    // staged stores: the output X[k0][k1b + 16 k1a][col] of every array as
+    // {512 floats, k1b (16), k1a (16, 16 rows apart), O*256 planes}
+    CUtensorMap omap = map;
+    int staged = 0;
+    if (staged_enabled() && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+        const cuuint64_t odims[4] = {512, 16, 16, (cuuint64_t)(O * 256)};
+        const cuuint64_t ostrides[3] = {256 * sizeof(float2), 16 * 256 * sizeof(float2),
+                                        65536 * sizeof(float2)};
+        const cuuint32_t obox[4] = {8, 1, 16, 16};
+        const cuuint32_t oestr[4] = {1, 1, 1, 1};
+        staged = enc(&omap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, out, odims, ostrides, obox, oestr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
     return launch_maybe_dependent(pipe_col_kernel<12, false, 3>, grid, 1024, col_smem<12>(), stream, flags & FLAG_PDL,
-                                  map, out, 256, 10, ntiles, tw.stage[12], tw.lo, tw.hi, tw.h, flags, status);
+                                  map, omap, out, 256, 10, ntiles, tw.stage[12], tw.lo, tw.hi, tw.h, flags, staged,
+                                  status);
 }
 
 template <int LOGN>
