@@ -332,6 +332,7 @@ def batched_report(torch, moafft, inputs, dev, iters):
     f = sum(flops((n,)) for n in lengths)
     alg = 16.0 * sum(lengths)
     bp = moafft.BatchedPlan(lengths, -1)
+    choice = bp.choice()
     t_batch = graph_time_ms(torch, lambda st: bp.exec(x, out, stream=st), iters)
     bp.destroy()
     # per-size baseline: the transforms of each length contiguous, one plan each
@@ -354,7 +355,7 @@ def batched_report(torch, moafft, inputs, dev, iters):
             raise RuntimeError("device status word set in the per-size baseline")
         p.destroy()
     return {"workload": "4096 x 1-D 2^k, k ~ U{6..16} (seed 2), N(0,1), complex64 forward",
-            "algorithmic_bytes": alg,
+            "plan": choice, "algorithmic_bytes": alg,
             "persistent_graph_us": t_batch * 1e3, "persistent_GFLOPs": f / t_batch / 1e6,
             "persistent_algorithmic_GBps": alg / t_batch / 1e6,
             "per_size_graph_us": t_size * 1e3, "per_size_launches": len(blocks),
@@ -545,9 +546,10 @@ def run_moa(args):
         torch.distributed.barrier()
     moafft.lib()
 
-    plans, xs, outs, pass_kernels, pass_bytes = [], [], [], {}, {}
+    plans, xs, outs, pass_kernels, pass_bytes, choices = [], [], [], {}, {}, {}
     for name, shape in WORKLOAD:
         p = moafft.Plan(list(shape), 1, -1)
+        choices[name] = p.choice()   # which candidate the autotuner kept, and why
         pass_kernels[name] = [p.pass_info(i)["kernel"] for i in range(p.info()["passes"])]
         for i, kname in enumerate(pass_kernels[name]):
             # algorithmic bytes of one launch: 16 per element and pass it does
@@ -760,7 +762,7 @@ def run_moa(args):
                 "config": {"workload": WORKLOAD_NAME, "l2": "inputs larger than L2 (128 MiB each), no flush",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "passes_per_step": launches_per_step},
-                "kernels": kernels, "tensor_core": tensor_core, "batched_uneven": batched, "autograd": autograd,
+                "plans": choices, "kernels": kernels, "tensor_core": tensor_core, "batched_uneven": batched, "autograd": autograd,
                 "small_1d": small, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches_per_step * args.steps, "rel_l2": parity or None,
                 "parity_ok": (all(v <= TOL for v in parity.values()) if parity else None),

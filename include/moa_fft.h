@@ -175,6 +175,14 @@ MOA_API const char *moa_fft_error_string(moa_status_t status);
 MOA_API moa_status_t moa_fft_plan_info(moa_fft_plan_t plan, int *passes, int64_t *split_r,
                                int64_t *split_c, size_t *workspace_bytes);
 
+/* What the plan chose and why: the r x c split, the tile size of the
+ * generic passes and the kernels of every pass (for a batched plan, the
+ * split offset of each large length), then where the choice came from
+ * (defaults or environment overrides, the autotuner, or its cache), written
+ * NUL-terminated into text[0..text_len-1] (truncated if needed).
+ * Instrumentation, so that a benchmark can state which candidate won. */
+MOA_API moa_status_t moa_fft_plan_choice(moa_fft_plan_t plan, char *text, size_t text_len);
+
 /* Describe pass `index` of the plan (0 <= index < passes): the name of the
  * kernel it launches, written NUL-terminated into name[0..name_len-1]
  * (truncated if needed; name may be NULL when name_len is 0), and its

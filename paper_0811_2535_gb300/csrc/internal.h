@@ -30,9 +30,11 @@ enum PassFlags {
 
 // Transforms per tile that a plan gives a column pass of 2^logN points over
 // C columns, and a row pass over O rows (transposed: its store is the
-// four-step transpose); the allocation-free entry point uses the same.
-int pick_logF_col(int logN, int64_t C);
-int pick_logF_row(int logN, int64_t O, bool transposed);
+// four-step transpose), for tiles of 2^tile points (10..14; anything else:
+// the default, 2^12 or MOA_TILE_LOG2); the allocation-free entry point uses
+// the same.
+int pick_logF_col(int logN, int64_t C, int tile = -1);
+int pick_logF_row(int logN, int64_t O, bool transposed, int tile = -1);
 
 // One kernel launch: N-point transforms (N = 2^logN <= 4096) along one axis.
 //  PASS_COL: view [O][N][C] (row-major), transform along the middle axis,

@@ -60,7 +60,10 @@ struct moa_fft_plan_s {
     // choices an autotuner (or an override) may fix: -1 / 0 = default
     int opt_lr = -1;              // log2 r of a lifted 1-D transform
     int opt_pipe = -1;            // 0: generic kernels only, 1: pipelined strided kernels allowed
-    int opt_batch_dlr = 0;        // batched: log2 r offset from floor(log2 n / 2)
+    int opt_batch_dlr[17] = {0};  // batched: per log2 length, log2 r offset from floor(log2 n / 2)
+    int opt_tile = -1;            // log2 of the tile of the generic passes (10..14)
+    int opt_3d2 = -1;             // 3-D 256^3: 1 = two passes, 0 = one pass per axis
+    std::string how;              // where the choices came from (defaults, autotuner, its cache)
     int opt_lift3 = -1;           // 1-D: 1 = three-level lift (r = 256, fused second/third pass)
     bool fault_wait = false;      // MOA_FAULT_WAIT=1 at plan time (tests): short device waits
     bool tma = false;             // tensor-map encoder present: pipelined kernels and the two-pass 3-D plan allowed
@@ -114,11 +117,13 @@ int tile_log2()
 
 int threads_log2_per_transform(int logN) { return logN < 4 ? 0 : logN - 4; }
 
+int tile_or_default(int tile) { return tile >= 10 && tile <= 14 ? tile : tile_log2(); }
+
 }  // namespace
 
-int moa::pick_logF_col(int logN, int64_t C)
+int moa::pick_logF_col(int logN, int64_t C, int tile)
 {
-    int lf = tile_log2() - logN;
+    int lf = tile_or_default(tile) - logN;
     if (lf < 2)
         lf = 2;
     if (lf > moa::max_logF_interleaved(logN))
@@ -132,9 +137,9 @@ int moa::pick_logF_col(int logN, int64_t C)
     return lf < 0 ? 0 : lf;
 }
 
-int moa::pick_logF_row(int logN, int64_t O, bool transposed)
+int moa::pick_logF_row(int logN, int64_t O, bool transposed, int tile)
 {
-    int lf = tile_log2() - logN;
+    int lf = tile_or_default(tile) - logN;
     if (transposed && lf < 2)
         lf = 2;
     if (transposed && lf > moa::max_logF_interleaved(logN))
@@ -152,7 +157,7 @@ int moa::pick_logF_row(int logN, int64_t O, bool transposed)
 
 namespace {
 
-PassDesc row_pass(int logN, int64_t O, int64_t Rt, int src, int dst)
+PassDesc row_pass(int logN, int64_t O, int64_t Rt, int src, int dst, int tile)
 {
     PassDesc d{};
     d.kind = moa::PASS_ROW;
@@ -160,14 +165,14 @@ PassDesc row_pass(int logN, int64_t O, int64_t Rt, int src, int dst)
     d.O = O;
     d.C = 1;
     d.Rt = Rt;
-    d.logF = moa::pick_logF_row(logN, O, Rt > 1);
+    d.logF = moa::pick_logF_row(logN, O, Rt > 1, tile);
     d.src = src;
     d.dst = dst;
     d.tw4 = 0;
     return d;
 }
 
-PassDesc col_pass(int logN, int64_t O, int64_t C, int tw4, int src, int dst)
+PassDesc col_pass(int logN, int64_t O, int64_t C, int tw4, int src, int dst, int tile)
 {
     PassDesc d{};
     d.kind = moa::PASS_COL;
@@ -175,7 +180,7 @@ PassDesc col_pass(int logN, int64_t O, int64_t C, int tw4, int src, int dst)
     d.O = O;
     d.C = C;
     d.Rt = 1;
-    d.logF = moa::pick_logF_col(logN, C);
+    d.logF = moa::pick_logF_col(logN, C, tile);
     d.src = src;
     d.dst = dst;
     d.tw4 = tw4;
@@ -233,7 +238,7 @@ moa_status_t build_passes(moa_fft_plan_s *p)
         const int64_t n = p->n[0];
         const int L = ilog2(n);
         if (L <= 12) {
-            p->passes.push_back(row_pass(L, B, 1, BUF_IN, BUF_OUT));
+            p->passes.push_back(row_pass(L, B, 1, BUF_IN, BUF_OUT, p->opt_tile));
             return MOA_OK;
         }
         // three-level lift: r = 256 columns pass, then the c = n / 256 point
@@ -244,7 +249,7 @@ moa_status_t build_passes(moa_fft_plan_s *p)
             const int lc = L - 8;
             p->split_r = 256;
             p->split_c = int64_t(1) << lc;
-            p->passes.push_back(col_pass(8, B, p->split_c, 1, BUF_IN, BUF_WS));
+            p->passes.push_back(col_pass(8, B, p->split_c, 1, BUF_IN, BUF_WS, p->opt_tile));
             PassDesc d{};
             d.kind = moa::PASS_LIFT3;
             d.logF = (lc + 1) / 2;   // cA
@@ -264,8 +269,8 @@ moa_status_t build_passes(moa_fft_plan_s *p)
         const int lc = L - lr;
         p->split_r = int64_t(1) << lr;
         p->split_c = int64_t(1) << lc;
-        p->passes.push_back(col_pass(lr, B, p->split_c, 1, BUF_IN, BUF_WS));
-        p->passes.push_back(row_pass(lc, B * p->split_r, p->split_r, BUF_WS, BUF_OUT));
+        p->passes.push_back(col_pass(lr, B, p->split_c, 1, BUF_IN, BUF_WS, p->opt_tile));
+        p->passes.push_back(row_pass(lc, B * p->split_r, p->split_r, BUF_WS, BUF_OUT, p->opt_tile));
         p->workspace_bytes = (size_t)p->total * sizeof(float2);
         return MOA_OK;
     }
@@ -275,7 +280,7 @@ moa_status_t build_passes(moa_fft_plan_s *p)
     // MOA_3D_TWO_PASS=0 keeps one pass per axis.
     const int pipe_mode = p->opt_pipe >= 0 ? p->opt_pipe : env_int("MOA_PIPE", 2);
     if (p->dims == 3 && p->n[0] == 256 && p->n[1] == 256 && p->n[2] == 256 && pipe_mode > 0 && p->tma &&
-        env_int("MOA_3D_TWO_PASS", 1) != 0) {
+        (p->opt_3d2 >= 0 ? p->opt_3d2 == 1 : env_int("MOA_3D_TWO_PASS", 1) != 0)) {
         PassDesc d1{};
         d1.kind = moa::PASS_PLANE1;
         d1.logN = 8;
@@ -297,14 +302,14 @@ moa_status_t build_passes(moa_fft_plan_s *p)
     // multi-D: last axis as rows, then every other axis as columns, in place
     const int d = p->dims;
     int src = BUF_IN;
-    p->passes.push_back(row_pass(ilog2(p->n[d - 1]), p->total / p->n[d - 1], 1, src, BUF_OUT));
+    p->passes.push_back(row_pass(ilog2(p->n[d - 1]), p->total / p->n[d - 1], 1, src, BUF_OUT, p->opt_tile));
     for (int a = d - 2; a >= 0; --a) {
         int64_t inner = 1, outer = B;
         for (int k = a + 1; k < d; ++k)
             inner *= p->n[k];
         for (int k = 0; k < a; ++k)
             outer *= p->n[k];
-        p->passes.push_back(col_pass(ilog2(p->n[a]), outer, inner, 0, BUF_OUT, BUF_OUT));
+        p->passes.push_back(col_pass(ilog2(p->n[a]), outer, inner, 0, BUF_OUT, BUF_OUT, p->opt_tile));
     }
     return MOA_OK;
 }
@@ -550,7 +555,7 @@ struct BatchQueue {
     bool has_large = false;
 };
 
-void build_queue(const int64_t *lengths, int64_t count, int dlr, int64_t resident, BatchQueue &bq)
+void build_queue(const int64_t *lengths, int64_t count, const int *dlr, int64_t resident, BatchQueue &bq)
 {
     std::vector<int64_t> offset(count);
     int64_t total = 0;
@@ -577,7 +582,7 @@ void build_queue(const int64_t *lengths, int64_t count, int dlr, int64_t residen
         const int first = (int)offs_sorted.size();
         offs_sorted.insert(offs_sorted.end(), group.begin(), group.end());
         if (logn >= 13) {
-            const int lr = batched_logr(logn, dlr);
+            const int lr = batched_logr(logn, dlr[logn]);
             need_stage[lr] = need_stage[logn - lr] = true;
             need_lift[logn] = true;
             for (size_t k = 0; k < group.size(); ++k) {
@@ -608,12 +613,12 @@ void build_queue(const int64_t *lengths, int64_t count, int dlr, int64_t residen
         size_t next_pending = 0;
         int64_t emitted_cols = 0;
         auto emit_rows = [&](size_t li) {
-            const int logn = large_logn[li], lr = batched_logr(logn, dlr);
+            const int logn = large_logn[li], lr = batched_logr(logn, dlr[logn]);
             for (int g = 0; g < (1 << (logn - 12)); ++g)
                 queue.push_back(moa::BatchTask{large[li], 1, (int16_t)g, (int8_t)logn, (int8_t)lr, 2, 0});
         };
         for (size_t li = 0; li < large.size(); ++li) {
-            const int logn = large_logn[li], lr = batched_logr(logn, dlr);
+            const int logn = large_logn[li], lr = batched_logr(logn, dlr[logn]);
             for (int g = 0; g < (1 << (logn - 12)); ++g) {
                 queue.push_back(moa::BatchTask{large[li], 1, (int16_t)g, (int8_t)logn, (int8_t)lr, 1, 0});
                 ++emitted_cols;
@@ -1017,8 +1022,14 @@ void log_plan(const moa_fft_plan_s *p, const char *how)
             passes.c_str());
 }
 
+// Choices a plan may have fixed (the autotuner's candidates); -1 = default
+// or environment override.
+struct PlanOpts {
+    int lr = -1, pipe = -1, lift3 = -1, tile = -1, two_pass3d = -1;
+};
+
 moa_status_t make_plan(moa_fft_plan_s **out, const int64_t *n, int dims, int64_t batch, int sign, int dtype,
-                       int64_t total, int opt_lr, int opt_pipe, int opt_lift3 = -1)
+                       int64_t total, const PlanOpts &o)
 {
     *out = nullptr;
     moa_fft_plan_s *p = new (std::nothrow) moa_fft_plan_s();
@@ -1031,9 +1042,11 @@ moa_status_t make_plan(moa_fft_plan_s **out, const int64_t *n, int dims, int64_t
     p->sign = sign;
     p->dtype = dtype;
     p->total = total;
-    p->opt_lr = opt_lr;
-    p->opt_pipe = opt_pipe;
-    p->opt_lift3 = opt_lift3;
+    p->opt_lr = o.lr;
+    p->opt_pipe = o.pipe;
+    p->opt_lift3 = o.lift3;
+    p->opt_tile = o.tile;
+    p->opt_3d2 = o.two_pass3d;
     p->tma = moa::pipe_supported();
     p->fault_wait = env_int("MOA_FAULT_WAIT", 0) == 1;
     moa_status_t st = build_passes(p);
@@ -1051,7 +1064,7 @@ moa_status_t make_plan(moa_fft_plan_s **out, const int64_t *n, int dims, int64_t
 }
 
 moa_status_t make_batched(moa_fft_plan_s **out, const int64_t *lengths, int64_t count, int sign, int dtype,
-                          int dlr)
+                          const int *dlr)
 {
     *out = nullptr;
     moa_fft_plan_s *p = new (std::nothrow) moa_fft_plan_s();
@@ -1059,7 +1072,8 @@ moa_status_t make_batched(moa_fft_plan_s **out, const int64_t *lengths, int64_t 
         return MOA_ERR_ALLOC;
     p->sign = sign;
     p->dtype = dtype;
-    p->opt_batch_dlr = dlr;
+    for (int l = 0; l <= 16; ++l)
+        p->opt_batch_dlr[l] = dlr[l];
     const moa_status_t st = build_batched(p, lengths, count);
     if (st != MOA_OK) {
         free_plan_memory(p);
@@ -1068,6 +1082,38 @@ moa_status_t make_batched(moa_fft_plan_s **out, const int64_t *lengths, int64_t 
     }
     *out = p;
     return MOA_OK;
+}
+
+// What distinguishes two plans for timing: every pass's kernel and tile.
+std::string plan_signature(const moa_fft_plan_s *p)
+{
+    std::string sig;
+    for (const PassDesc &d : p->passes) {
+        char buf[96];
+        pass_name(p, d, buf, sizeof(buf));
+        sig += std::string(buf) + "/" + std::to_string(d.logF) + ";";
+    }
+    return sig;
+}
+
+// Short description of a plan's choices (log lines and moa_fft_plan_choice).
+std::string plan_choice(const moa_fft_plan_s *p)
+{
+    std::string c;
+    if (p->batched) {
+        c = "batched: log2 r offset per length";
+        for (int l = 13; l <= 16; ++l)
+            c += " 2^" + std::to_string(l) + ":" + std::to_string(p->opt_batch_dlr[l]);
+    } else {
+        c = "split r=" + std::to_string((long long)p->split_r) + " c=" + std::to_string((long long)p->split_c) +
+            ", tile 2^" + std::to_string(tile_or_default(p->opt_tile)) + ", passes ";
+        for (size_t i = 0; i < p->passes.size(); ++i) {
+            char buf[96];
+            pass_name(p, p->passes[i], buf, sizeof(buf));
+            c += (i ? " -> " : "") + std::string(buf);
+        }
+    }
+    return c + " (" + p->how + ")";
 }
 
 }  // namespace
@@ -1108,81 +1154,106 @@ moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int6
     if (const moa_status_t vs = validate_request(n, dims, batch, sign, dtype, &total))
         return vs;
 
-    int opt_lr = -1, opt_pipe = -1, opt_lift3 = -1;
+    // The autotuner (Sec. 4.8: every breakpoint is correct; the choice is
+    // made by timing, as the paper's script-based search does): every
+    // admissible r x c split of a lifted 1-D transform and its three-level
+    // lift, the pipelined or generic strided kernels, the tile size of the
+    // generic passes, and for 256^3 arrays the two-pass or per-axis form.
+    // Candidates that build the same passes are timed once.  A choice fixed
+    // by an environment override is not searched.
+    PlanOpts best_opts;
     const int L = ilog2(n[0]);
-    const char *how = "defaults or environment overrides";
-    if (dims == 1 && L > 12 && autotune_enabled() && !env_set("MOA_SPLIT_LOG2R") && !env_set("MOA_LIFT3")) {
-        const std::string key = device_tag() + ":1d3:" + std::to_string(L) + ":" + std::to_string(batch);
+    std::string how = "defaults or environment overrides";
+    const bool lifted = dims == 1 && L > 12;
+    const bool tunable = dtype == MOA_C64 && autotune_enabled() && (dims > 1 || lifted || batch > 1);
+    if (tunable) {
+        // the key names the choices fixed by environment overrides, which
+        // are not searched (their cached entry holds -1 = default there)
+        std::string key = device_tag() + ":plan:" + std::to_string(dims);
+        for (int i = 0; i < dims; ++i)
+            key += ":" + std::to_string((long long)n[i]);
+        key += ":" + std::to_string((long long)batch) + ":";
+        const char *fixed[] = {"MOA_SPLIT_LOG2R", "MOA_LIFT3", "MOA_PIPE", "MOA_TILE_LOG2", "MOA_3D_TWO_PASS"};
+        for (int i = 0; i < 5; ++i)
+            key += env_set(fixed[i]) ? "f" : "s";
         std::string v;
-        if (tune_get(key, v) && sscanf(v.c_str(), "%d %d %d", &opt_lr, &opt_pipe, &opt_lift3) == 3) {
+        PlanOpts c;
+        if (tune_get(key, v) && sscanf(v.c_str(), "%d %d %d %d %d", &c.lr, &c.pipe, &c.lift3, &c.tile,
+                                       &c.two_pass3d) == 5) {
+            best_opts = c;
             how = "autotuner choice from the cache";
         } else {
             how = "autotuned";
-            float best = INFINITY;
-            const bool try_generic = !env_set("MOA_PIPE");
-            for (int lr = std::max(1, L - 12); lr <= std::min(12, L - 1); ++lr) {
-                for (int pipe = 2; pipe >= (try_generic ? 0 : 2); --pipe) {
-                    moa_fft_plan_s *cand = nullptr;
-                    const moa_status_t st =
-                        make_plan(&cand, n, dims, batch, sign, dtype, total, lr, try_generic ? pipe : -1, 0);
-                    if (st != MOA_OK)
-                        return st;
-                    const bool used_blk = std::any_of(cand->passes.begin(), cand->passes.end(),
-                                                      [](const PassDesc &d) { return d.blk != 0; });
-                    if (try_generic && pipe == 2 && !used_blk) {
-                        free_plan_memory(cand);
-                        delete cand;
-                        continue;   // same plan as pipe = 1
-                    }
-                    const float ms = time_exec(cand);
-                    if (log_enabled())
-                        fprintf(stderr, "moafft: autotune 1-D 2^%d x %lld: log2 r = %d, pipe mode %d: %.1f us\n", L,
-                                (long long)batch, lr, pipe, ms * 1e3f);
-                    const bool used_pipe = std::any_of(cand->passes.begin(), cand->passes.end(),
-                                                       [](const PassDesc &d) { return d.pipe != 0; });
-                    free_plan_memory(cand);
-                    delete cand;
-                    if (ms < best) {
-                        best = ms;
-                        opt_lr = lr;
-                        opt_pipe = try_generic ? pipe : -1;
-                        opt_lift3 = 0;
-                    }
-                    if (!used_pipe)
-                        break;   // no pass of this split has a pipelined form
-                }
+            std::vector<int> lrs{-1}, pipes{-1}, lift3s{-1}, tiles{-1}, twos{-1};
+            if (lifted && !env_set("MOA_SPLIT_LOG2R") && !env_set("MOA_LIFT3")) {
+                lrs.clear();
+                for (int lr = std::max(1, L - 12); lr <= std::min(12, L - 1); ++lr)
+                    lrs.push_back(lr);
+                lift3s = {0};
             }
-            // the three-level lift (r = 256, fused second and third pass)
-            if (L >= 21 && L <= 24) {
+            if (!env_set("MOA_PIPE"))
+                pipes = {2, 1, 0};
+            if (!env_set("MOA_TILE_LOG2"))
+                tiles = {12, 11, 13};
+            if (dims == 3 && !env_set("MOA_3D_TWO_PASS"))
+                twos = {1, 0};
+            std::vector<PlanOpts> cands;
+            for (int lr : lrs)
+                for (int pipe : pipes)
+                    for (int tile : tiles)
+                        for (int two : twos) {
+                            PlanOpts o;
+                            o.lr = lr;
+                            o.pipe = pipe;
+                            o.lift3 = lift3s[0];
+                            o.tile = tile;
+                            o.two_pass3d = two;
+                            cands.push_back(o);
+                        }
+            if (lifted && L >= 21 && L <= 24 && !env_set("MOA_SPLIT_LOG2R") && !env_set("MOA_LIFT3"))
+                for (int tile : tiles) {
+                    PlanOpts o;
+                    o.lift3 = 1;
+                    o.tile = tile;
+                    cands.push_back(o);
+                }
+            float best = INFINITY;
+            std::set<std::string> seen;
+            for (const PlanOpts &o : cands) {
                 moa_fft_plan_s *cand = nullptr;
-                const moa_status_t st = make_plan(&cand, n, dims, batch, sign, dtype, total, -1, -1, 1);
-                if (st == MOA_OK) {
-                    const float ms = time_exec(cand);
-                    if (log_enabled())
-                        fprintf(stderr, "moafft: autotune 1-D 2^%d x %lld: three-level lift: %.1f us\n", L,
-                                (long long)batch, ms * 1e3f);
+                const moa_status_t st = make_plan(&cand, n, dims, batch, sign, dtype, total, o);
+                if (st == MOA_ERR_UNSUPPORTED)
+                    continue;
+                if (st != MOA_OK)
+                    return st;
+                const std::string sig = plan_signature(cand);
+                if (!seen.insert(sig).second) {   // the same passes as a candidate already timed
                     free_plan_memory(cand);
                     delete cand;
-                    if (ms < best) {
-                        best = ms;
-                        opt_lr = -1;
-                        opt_pipe = -1;
-                        opt_lift3 = 1;
-                    }
-                } else if (st != MOA_ERR_UNSUPPORTED) {
-                    return st;
+                    continue;
+                }
+                const float ms = time_exec(cand);
+                if (log_enabled())
+                    fprintf(stderr, "moafft: autotune candidate %s: %.1f us\n", sig.c_str(), ms * 1e3f);
+                free_plan_memory(cand);
+                delete cand;
+                if (ms < best) {
+                    best = ms;
+                    best_opts = o;
                 }
             }
             if (std::isfinite(best))
-                tune_put(key, std::to_string(opt_lr) + " " + std::to_string(opt_pipe) + " " +
-                                  std::to_string(opt_lift3));
+                tune_put(key, std::to_string(best_opts.lr) + " " + std::to_string(best_opts.pipe) + " " +
+                                  std::to_string(best_opts.lift3) + " " + std::to_string(best_opts.tile) + " " +
+                                  std::to_string(best_opts.two_pass3d));
         }
     }
     moa_fft_plan_s *p = nullptr;
-    const moa_status_t st = make_plan(&p, n, dims, batch, sign, dtype, total, opt_lr, opt_pipe, opt_lift3);
+    const moa_status_t st = make_plan(&p, n, dims, batch, sign, dtype, total, best_opts);
     if (st != MOA_OK)
         return st;
-    log_plan(p, how);
+    p->how = how;
+    log_plan(p, how.c_str());
     {
         std::lock_guard<std::mutex> lk(g_plans_mu);
         g_plans.insert(p);
@@ -1213,45 +1284,73 @@ moa_status_t moa_fft_plan_batched(moa_fft_plan_t *plan, const int64_t *lengths, 
     }
     if (dtype != MOA_C64)
         return MOA_ERR_UNSUPPORTED;
-    int dlr = 0;
-    bool any_large = false;
+    // per-length split of the large transforms (log2 r offset -1, 0 or +1
+    // from floor(log2 n / 2)), one length at a time, the others held at their
+    // best so far
+    int dlr[17] = {0};
     int hist[17] = {0};
-    for (int64_t i = 0; i < count; ++i) {
+    for (int64_t i = 0; i < count; ++i)
         hist[ilog2(lengths[i])]++;
-        any_large |= lengths[i] > 4096;
-    }
+    const bool any_large = hist[13] + hist[14] + hist[15] + hist[16] > 0;
+    std::string how = "default split of the large transforms";
     if (any_large && autotune_enabled() && !env_set("MOA_BATCH_LOG2R")) {
-        std::string key = device_tag() + ":batched:";
+        std::string key = device_tag() + ":batched2:";
         for (int l = 1; l <= 16; ++l)
             key += std::to_string(hist[l]) + (l < 16 ? "," : "");
         std::string v;
-        if (!(tune_get(key, v) && sscanf(v.c_str(), "%d", &dlr) == 1)) {
-            float best = INFINITY;
-            for (int cand_dlr = -1; cand_dlr <= 1; ++cand_dlr) {
+        int c[4];
+        if (tune_get(key, v) && sscanf(v.c_str(), "%d %d %d %d", &c[0], &c[1], &c[2], &c[3]) == 4) {
+            for (int l = 13; l <= 16; ++l)
+                dlr[l] = c[l - 13];
+            how = "autotuner choice from the cache";
+        } else {
+            how = "autotuned";
+            auto timed = [&](const int *off, float &ms) -> moa_status_t {
                 moa_fft_plan_s *cand = nullptr;
-                const moa_status_t st = make_batched(&cand, lengths, count, sign, dtype, cand_dlr);
+                const moa_status_t st = make_batched(&cand, lengths, count, sign, dtype, off);
                 if (st != MOA_OK)
                     return st;
-                const float ms = time_exec(cand);
+                ms = time_exec(cand);
                 if (log_enabled())
-                    fprintf(stderr, "moafft: autotune batched (%lld transforms): log2 r offset %+d: %.1f us\n",
-                            (long long)count, cand_dlr, ms * 1e3f);
+                    fprintf(stderr,
+                            "moafft: autotune batched (%lld transforms): log2 r offsets 2^13:%+d 2^14:%+d 2^15:%+d "
+                            "2^16:%+d: %.1f us\n",
+                            (long long)count, off[13], off[14], off[15], off[16], ms * 1e3f);
                 free_plan_memory(cand);
                 delete cand;
-                if (ms < best) {
-                    best = ms;
-                    dlr = cand_dlr;
+                return MOA_OK;
+            };
+            float best = INFINITY;
+            moa_status_t st = timed(dlr, best);
+            if (st != MOA_OK)
+                return st;
+            for (int l = 13; l <= 16; ++l) {
+                if (hist[l] == 0)
+                    continue;
+                for (int d = -1; d <= 1; d += 2) {
+                    int off[17];
+                    std::copy(dlr, dlr + 17, off);
+                    off[l] = d;
+                    float ms = INFINITY;
+                    if ((st = timed(off, ms)) != MOA_OK)
+                        return st;
+                    if (ms < best) {
+                        best = ms;
+                        dlr[l] = d;
+                    }
                 }
             }
             if (std::isfinite(best))
-                tune_put(key, std::to_string(dlr));
+                tune_put(key, std::to_string(dlr[13]) + " " + std::to_string(dlr[14]) + " " +
+                                  std::to_string(dlr[15]) + " " + std::to_string(dlr[16]));
         }
     }
     moa_fft_plan_s *p = nullptr;
     const moa_status_t st = make_batched(&p, lengths, count, sign, dtype, dlr);
     if (st != MOA_OK)
         return st;
-    log_plan(p, dlr != 0 ? "log2 r offset from the autotuner" : "default split of the large transforms");
+    p->how = how;
+    log_plan(p, how.c_str());
     {
         std::lock_guard<std::mutex> lk(g_plans_mu);
         g_plans.insert(p);
@@ -1348,6 +1447,15 @@ moa_status_t moa_fft_plan_info(moa_fft_plan_t plan, int *passes, int64_t *split_
     return MOA_OK;
 }
 
+moa_status_t moa_fft_plan_choice(moa_fft_plan_t plan, char *text, size_t text_len)
+{
+    if (!is_live(plan) || !text || text_len == 0)
+        return MOA_ERR_INVALID_ARG;
+    const std::string c = plan_choice(plan);
+    snprintf(text, text_len, "%s", c.c_str());
+    return MOA_OK;
+}
+
 moa_status_t moa_fft_pass_info(moa_fft_plan_t plan, int index, char *name, size_t name_len, int64_t *bytes)
 {
     if (!is_live(plan) || index < 0 || (size_t)index >= (plan->batched ? 1 : plan->passes.size()))
@@ -1382,7 +1490,8 @@ moa_status_t moa_fft_batched_queue(const int64_t *lengths, int64_t count, int64_
             return MOA_ERR_UNSUPPORTED;
     }
     BatchQueue bq;
-    build_queue(lengths, count, 0, resident, bq);
+    const int no_offsets[17] = {0};
+    build_queue(lengths, count, no_offsets, resident, bq);
     const int64_t nt = (int64_t)bq.queue.size();
     if (ntasks)
         *ntasks = nt;

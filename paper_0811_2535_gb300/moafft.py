@@ -42,6 +42,7 @@ SIGNATURES = {
     "moa_fft_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64),
                                          ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_size_t)]),
     "moa_fft_pass_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(_I64)]),
+    "moa_fft_plan_choice": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     "moa_fft_estimate": (ctypes.c_int, [ctypes.POINTER(_I64), ctypes.c_int, _I64, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                         ctypes.POINTER(ctypes.c_size_t), ctypes.c_char_p, ctypes.c_size_t]),
@@ -194,6 +195,12 @@ class Plan:
         _check(lib().moa_fft_plan_info(self._h, ctypes.byref(p), ctypes.byref(r), ctypes.byref(c), ctypes.byref(w)),
                "moa_fft_plan_info")
         return {"passes": p.value, "split_r": r.value, "split_c": c.value, "workspace_bytes": w.value}
+
+    def choice(self) -> str:
+        """The plan's split, tile and kernels, and where they came from."""
+        buf = ctypes.create_string_buffer(512)
+        _check(lib().moa_fft_plan_choice(self._h, buf, 512), "moa_fft_plan_choice")
+        return buf.value.decode()
 
     def pass_info(self, index: int) -> dict:
         """Kernel name and algorithmic bytes of pass ``index``."""

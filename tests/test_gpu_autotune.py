@@ -1,7 +1,10 @@
 """Plan-time autotuner (GPU): it times the admissible r x c splits of a
-lifted 1-D transform (and the split policy of a batched plan), keeps the
-fastest, records the choice in its cache file and reuses it; results stay
-within the parity tolerance whatever it picks."""
+lifted 1-D transform and its three-level lift, the pipelined or generic
+strided kernels, the tile size of the generic passes, the two-pass or
+per-axis form of 256^3 arrays, and the per-length split of a batched plan;
+it keeps the fastest, records the choice in its cache file and reuses it;
+results stay within the parity tolerance whatever it picks, and the plan
+states its choice (moa_fft_plan_choice)."""
 import os
 import time
 
@@ -39,11 +42,13 @@ def test_autotuned_split_is_cached_and_correct(env, tmp_path, monkeypatch):
     t_first = time.perf_counter() - t0
     info = plan.info()
     text = cache.read_text()
-    line = [ln for ln in text.splitlines() if ":1d3:19:3 " in ln]
+    line = [ln for ln in text.splitlines() if ":plan:1:524288:3:sssss " in ln]
     assert len(line) == 1, text
-    lr, pipe, lift3 = (int(v) for v in line[0].split()[1:4])
+    lr, pipe, lift3, tile, two = (int(v) for v in line[0].split()[1:6])
     assert lift3 == 0          # the three-level lift is a candidate from 2^21 on
     assert info["split_r"] == 1 << lr and 7 <= lr <= 12
+    assert tile in (11, 12, 13) and two == -1
+    assert "autotuned" in plan.choice() and ("r=%d" % (1 << lr)) in plan.choice()
     x = inputs.uniform((3, n), 77)
     y = plan.exec(torch.from_numpy(x).cuda()).cpu().numpy()
     ref = oracle.fft_radix2(x.astype(np.complex128), -1)
@@ -54,6 +59,7 @@ def test_autotuned_split_is_cached_and_correct(env, tmp_path, monkeypatch):
     again = moafft.Plan([n], 3, -1)       # served from the cache: no timing runs
     t_second = time.perf_counter() - t0
     assert again.info()["split_r"] == info["split_r"]
+    assert "from the cache" in again.choice()
     assert t_second < t_first
     again.destroy()
 
@@ -68,7 +74,11 @@ def test_autotuned_batched_plan(env, tmp_path, monkeypatch):
     lengths = [1 << k for k in (14, 9, 16, 13, 6, 15, 12)]
     vecs = [inputs.uniform(n, 80 + i) for i, n in enumerate(lengths)]
     plan = moafft.BatchedPlan(lengths, -1)
-    assert ":batched:" in cache.read_text()
+    line = [ln for ln in cache.read_text().splitlines() if ":batched2:" in ln]
+    assert len(line) == 1
+    offsets = [int(v) for v in line[0].split()[1:5]]
+    assert all(o in (-1, 0, 1) for o in offsets)
+    assert "autotuned" in plan.choice() and "2^16:%d" % offsets[3] in plan.choice()
     x = torch.from_numpy(np.concatenate(vecs)).cuda()
     y = plan.exec(x).cpu().numpy()
     for o, n, v in zip(plan.offsets(), lengths, vecs):
@@ -93,11 +103,40 @@ def test_plan_log(env, tmp_path):
     res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=envv, timeout=300)
     assert res.returncode == 0, res.stderr
     lines = [ln for ln in res.stderr.splitlines() if ln.startswith("moafft: ")]
-    assert any(ln.startswith("moafft: autotune 1-D 2^17 x 2: log2 r = ") for ln in lines), lines
+    cands = [ln for ln in lines if ln.startswith("moafft: autotune candidate ")]
+    # 1-D 2^17: splits 2^5..2^12, with pipelined and generic kernels and three tiles
+    assert sum("col_pass_kernel<" in ln or "pipe_col_kernel<" in ln for ln in cands) >= 8, lines
+    # 2-D 64 x 32: the tile sizes of its two generic passes
+    assert any("row_pass_kernel<5,0>/" in ln and "col_pass_kernel<6,0>/" in ln for ln in cands), lines
     plan_lines = [ln for ln in lines if ln.startswith("moafft: plan ")]
     assert len(plan_lines) == 2, lines
     assert "131072 batch 2 sign -1" in plan_lines[0] and "autotuned" in plan_lines[0]
     assert "64x32 batch 1 sign +1" in plan_lines[1] and "row_pass_kernel<5,0> -> col_pass_kernel<6,0>" in plan_lines[1]
+    assert "autotuned" in plan_lines[1]
+
+
+@pytest.mark.parametrize("shape,batch", [((1 << 22,), 1), ((1 << 12,), 16), ((4096, 4096), 1),
+                                         ((512, 1024), 2), ((256, 256, 256), 1), ((64, 32, 128), 2)])
+def test_every_tuned_plan_kind_matches_oracle(env, shape, batch, tmp_path, monkeypatch):
+    """Lifted 1-D, batched 1-D rows, 2-D and 3-D plans, each tuned from an
+    empty cache: the chosen plan is stated and its output matches the FP64
+    oracle."""
+    torch, moafft, oracle = env
+    from paper_0811_2535_gb300 import inputs
+    monkeypatch.setenv("MOA_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    monkeypatch.setenv("MOA_AUTOTUNE", "1")
+    for k in ("MOA_SPLIT_LOG2R", "MOA_PIPE", "MOA_TILE_LOG2", "MOA_3D_TWO_PASS", "MOA_LIFT3"):
+        monkeypatch.delenv(k, raising=False)
+    plan = moafft.Plan(list(shape), batch, -1)
+    assert "autotuned" in plan.choice()
+    x = inputs.uniform((batch,) + tuple(shape), 90 + len(shape))
+    y = plan.exec(torch.from_numpy(x.reshape(-1)).cuda()).cpu().numpy().reshape(batch, -1)
+    assert plan.status() == 0
+    plan.destroy()
+    x64 = x.astype(np.complex128)
+    ref = (oracle.fft_radix2(x64, -1) if len(shape) == 1 else oracle.fft_nd(x64, len(shape), -1)).reshape(batch, -1)
+    err = np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= TOL
 
 
 @pytest.mark.parametrize("shape,batch,dtype", [((1 << 24,), 1, 0), ((1 << 19,), 2, 0), ((1 << 13,), 3, 0),

@@ -374,6 +374,7 @@ def test_3d_two_pass(env, batch, sign, monkeypatch):
     against one pass per axis (MOA_3D_TWO_PASS=0), and in place."""
     torch, moafft, _ = env
     from paper_0811_2535_gb300 import inputs
+    monkeypatch.setenv("MOA_3D_TWO_PASS", "1")
     shape = (256, 256, 256)
     x = inputs.uniform((batch,) + shape, 6800 + batch)
     plan = moafft.Plan(list(shape), batch, sign)
