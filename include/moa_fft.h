@@ -75,7 +75,11 @@ typedef enum {
 
 /* Create a plan for `batch` transforms of shape n[0..dims-1].
  *   n      : dims lengths, each a power of two >= 2 (t >= 1, Fig. 2.1).
- *            1-D: n[0] <= 2^24.  2-D/3-D: every n[i] <= 4096.
+ *            1-D: n[0] <= 2^30 (up to 2^24 in two passes, n = r*c
+ *            with r, c <= 4096; beyond, three passes, n = r1*r2*c).
+ *            2-D/3-D: every n[i] <= 2^24 (an axis above 4096 is lifted
+ *            L = L1*L2 inside the array, two passes for that axis, and the
+ *            plan then uses a workspace of the array's size).
  *   dims   : 1, 2 or 3.
  *   batch  : >= 1; batch * prod(n) < 2^31.
  *   sign   : -1 (forward, exp(-2 pi i jk/n)) or +1.

@@ -38,7 +38,14 @@ int pick_logF_row(int logN, int64_t O, bool transposed, int tile = -1);
 
 // One kernel launch: N-point transforms (N = 2^logN <= 4096) along one axis.
 //  PASS_COL: view [O][N][C] (row-major), transform along the middle axis,
-//            F consecutive columns per tile, output in the same view.
+//            F consecutive columns per tile, output in the same view; with
+//            Rt > 1 (a lifted axis, second half) output row k of o goes to
+//            row (o % Rt) + Rt*k of the [O/Rt][N*Rt][C] view.  The four-step
+//            twiddle (tw4) is w_M^((col / cdiv) * row), row the output row in
+//            that view and M = N * Rt * C / cdiv: with cdiv = 1, Rt = 1 the
+//            twiddle w_n^(j2*k1) of the lifted 1-D transform; with cdiv = the
+//            inner extent, the twiddle between the two halves of an axis
+//            lifted inside a multi-D array.
 //  PASS_ROW: view [O][N], transform along contiguous rows, F rows per tile;
 //            output row o, index k goes to (o / Rt)*(N*Rt) + (o % Rt) + Rt*k
 //            (Rt = 1: natural order; Rt = r: the four-step transpose).
@@ -55,12 +62,16 @@ struct PassDesc {
     int blk;        // blocked workspace of the lifted transform (pipe kernels only):
                     // 1 = pass 1 writes 4 x 4 blocks, 2 = pass 2 reads them
     int umma;       // PASS_TC: 1 = tcgen05 kernel (tc_umma.cu), 0 = mma.sync kernel
+    int cdiv;       // PASS_COL twiddle: column divisor (0 or 1: none)
+    int twlog;      // PASS_COL twiddle: log2 M of its table (0: the plan's main table lo/hi)
 };
 
 struct TwiddleSet {
     const float2 *stage[13];   // per logN: stage tables (Sched<logN> layout), or null
     const float2 *lo, *hi;     // two-level table of w_n^e: lo[e & (2^h-1)] * hi[e >> h]
     int h;
+    const float2 *xlo[32], *xhi[32];   // further two-level tables of w_M, by log2 M (lifted axes)
+    int xh[32];
     const float2 *tc;          // tensor-core path: per-stage full tables
 };
 

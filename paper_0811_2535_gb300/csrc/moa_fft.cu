@@ -263,6 +263,30 @@ moa_status_t build_passes(moa_fft_plan_s *p)
             p->workspace_bytes = (size_t)p->total * sizeof(float2);
             return MOA_OK;
         }
+        if (L > 24) {
+            // n = r*c with r = r1*r2 (Sec. 4.2 applied twice): every factor
+            // <= 4096.  Pass 1: r2-point DFTs over the slow index j1s of the
+            // rows (stride r1*c) with the twiddle w_r^(j1f*k1s), j1f = the
+            // column / c; pass 2: r1-point DFTs over j1f (stride c), the row
+            // k1 = k1s + r2*k1f stored in place of the natural r x c layout,
+            // with the four-step twiddle w_n^(j2*k1); pass 3: the c-point rows
+            // stored transposed at X[k1 + r*k2].
+            const int lc = (L + 2) / 3, lr = L - lc;
+            const int lr1 = (lr + 1) / 2, lr2 = lr - lr1;
+            const int64_t c = int64_t(1) << lc, r1 = int64_t(1) << lr1, r2 = int64_t(1) << lr2;
+            p->split_r = int64_t(1) << lr;
+            p->split_c = c;
+            PassDesc a = col_pass(lr2, B, r1 * c, 1, BUF_IN, BUF_OUT, p->opt_tile);
+            a.cdiv = (int)c;
+            a.twlog = lr;
+            PassDesc b = col_pass(lr1, B * r2, c, 1, BUF_OUT, BUF_WS, p->opt_tile);
+            b.Rt = r2;
+            p->passes.push_back(a);
+            p->passes.push_back(b);
+            p->passes.push_back(row_pass(lc, B * p->split_r, p->split_r, BUF_WS, BUF_OUT, p->opt_tile));
+            p->workspace_bytes = (size_t)p->total * sizeof(float2);
+            return MOA_OK;
+        }
         int lr = p->opt_lr >= 0 ? p->opt_lr : env_int("MOA_SPLIT_LOG2R", L / 2);
         if (lr < 1 || lr > 12 || L - lr < 1 || L - lr > 12)
             lr = L / 2;
@@ -299,8 +323,61 @@ moa_status_t build_passes(moa_fft_plan_s *p)
         p->workspace_bytes = (size_t)p->total * sizeof(float2);
         return MOA_OK;
     }
-    // multi-D: last axis as rows, then every other axis as columns, in place
     const int d = p->dims;
+    bool long_axis = false;
+    for (int a = 0; a < d; ++a)
+        long_axis |= p->n[a] > 4096;
+    if (long_axis) {
+        // An axis longer than 4096 is lifted L = L1*L2 (element j = js*L1 + jf)
+        // inside the array (Sec. 4.2 on one axis, Eq. B.6 on the others): an
+        // L2-point pass over js (stride L1*inner) with the twiddle
+        // w_L^(jf*ks), jf = the column / inner, then an L1-point pass over jf
+        // (stride inner) whose output row ks + L2*kf restores the natural
+        // layout.  The passes go through the workspace, the last one into
+        // `out`.
+        std::vector<PassDesc> ps;
+        for (int a = d - 1; a >= 0; --a) {
+            int64_t inner = 1, outer = B;
+            for (int k = a + 1; k < d; ++k)
+                inner *= p->n[k];
+            for (int k = 0; k < a; ++k)
+                outer *= p->n[k];
+            const int l = ilog2(p->n[a]);
+            if (l <= 12) {
+                ps.push_back(a == d - 1 ? row_pass(l, outer, 1, 0, 0, p->opt_tile)
+                                        : col_pass(l, outer, inner, 0, 0, 0, p->opt_tile));
+                continue;
+            }
+            const int l1 = (l + 1) / 2, l2 = l - l1;
+            const int64_t L1 = int64_t(1) << l1, L2 = int64_t(1) << l2;
+            PassDesc pa = col_pass(l2, outer, L1 * inner, 1, 0, 0, p->opt_tile);
+            pa.cdiv = (int)inner;
+            pa.twlog = l;
+            ps.push_back(pa);
+            if (inner == 1) {
+                ps.push_back(row_pass(l1, outer * L2, L2, 0, 0, p->opt_tile));
+            } else {
+                PassDesc pb = col_pass(l1, outer * L2, inner, 0, 0, 0, p->opt_tile);
+                pb.Rt = L2;
+                ps.push_back(pb);
+            }
+        }
+        // buffers: the last pass writes `out`, the ones before alternate
+        // between the workspace and `out`, the first reads `in` (the first
+        // pass keeps its own tiles' places, so in == out is allowed)
+        int dst = BUF_OUT;
+        for (size_t i = ps.size(); i-- > 0;) {
+            ps[i].dst = dst;
+            dst = dst == BUF_OUT ? BUF_WS : BUF_OUT;
+        }
+        ps[0].src = BUF_IN;
+        for (size_t i = 1; i < ps.size(); ++i)
+            ps[i].src = ps[i - 1].dst;
+        p->passes = ps;
+        p->workspace_bytes = (size_t)p->total * sizeof(float2);
+        return MOA_OK;
+    }
+    // multi-D: last axis as rows, then every other axis as columns, in place
     int src = BUF_IN;
     p->passes.push_back(row_pass(ilog2(p->n[d - 1]), p->total / p->n[d - 1], 1, src, BUF_OUT, p->opt_tile));
     for (int a = d - 2; a >= 0; --a) {
@@ -322,7 +399,10 @@ void assign_pipe(moa_fft_plan_s *p)
 {
     const int pipe_mode = p->tma ? (p->opt_pipe >= 0 ? p->opt_pipe : env_int("MOA_PIPE", 2)) : 0;
     for (PassDesc &d : p->passes) {
-        const bool strided4 = d.logN >= 10 && d.logN <= 12 && d.logF == 2 &&
+        // the pipelined kernels take the plain views: no lifted-axis twiddle,
+        // no transposed column store
+        const bool plain = d.cdiv <= 1 && d.twlog == 0 && (d.kind != moa::PASS_COL || d.Rt <= 1);
+        const bool strided4 = plain && d.logN >= 10 && d.logN <= 12 && d.logF == 2 &&
                               (d.kind == moa::PASS_COL ? d.C >= 4 : d.Rt > 1);
         d.pipe = 0;
         d.blk = 0;
@@ -447,6 +527,16 @@ moa_status_t allocate_and_fill(moa_fft_plan_s *p)
         hi_off = bytes;
         bytes += ((size_t(1) << (logn - h)) * sizeof(float2) + 255) & ~size_t(255);
     }
+    // further two-level tables w_M (lifted axes), one per order M
+    size_t x_lo_off[32] = {0}, x_hi_off[32] = {0};
+    for (const PassDesc &d : p->passes)
+        if (d.twlog > 0 && d.twlog < 32 && !x_lo_off[d.twlog]) {
+            const int xh = (d.twlog + 1) / 2;
+            x_lo_off[d.twlog] = bytes;
+            bytes += ((size_t(1) << xh) * sizeof(float2) + 255) & ~size_t(255);
+            x_hi_off[d.twlog] = bytes;
+            bytes += ((size_t(1) << (d.twlog - xh)) * sizeof(float2) + 255) & ~size_t(255);
+        }
     size_t w256_off = 0;
     for (const PassDesc &d : p->passes)
         if (d.kind == moa::PASS_PLANE1 && !w256_off) {
@@ -507,6 +597,20 @@ moa_status_t allocate_and_fill(moa_fft_plan_s *p)
         p->tw.lo = lo;
         p->tw.hi = hi;
         p->tw.h = h;
+    }
+    for (int l = 1; l < 32; ++l) {
+        p->tw.xlo[l] = p->tw.xhi[l] = nullptr;
+        p->tw.xh[l] = 0;
+        if (!x_lo_off[l])
+            continue;
+        const int xh = (l + 1) / 2;
+        float2 *lo = reinterpret_cast<float2 *>(base + x_lo_off[l]);
+        float2 *hi = reinterpret_cast<float2 *>(base + x_hi_off[l]);
+        if (moa::generate_two_level(lo, hi, l, xh, 0) != cudaSuccess)
+            return MOA_ERR_CUDA;
+        p->tw.xlo[l] = lo;
+        p->tw.xhi[l] = hi;
+        p->tw.xh[l] = xh;
     }
     for (const PassDesc &d : p->passes)
         if (d.kind == moa::PASS_LIFT3) {
@@ -1130,7 +1234,7 @@ moa_status_t validate_request(const int64_t *n, int dims, int64_t batch, int sig
     for (int i = 0; i < dims; ++i) {
         if (!pow2_ge2(n[i]))
             return MOA_ERR_INVALID_SIZE;
-        if (dims == 1 ? n[i] > (int64_t(1) << 24) : n[i] > 4096)
+        if (n[i] > (int64_t(1) << (dims == 1 ? 30 : 24)))
             return MOA_ERR_UNSUPPORTED;
         t *= n[i];
         if (t >= (int64_t(1) << 31))
@@ -1185,7 +1289,7 @@ moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int6
         } else {
             how = "autotuned";
             std::vector<int> lrs{-1}, pipes{-1}, lift3s{-1}, tiles{-1}, twos{-1};
-            if (lifted && !env_set("MOA_SPLIT_LOG2R") && !env_set("MOA_LIFT3")) {
+            if (lifted && L <= 24 && !env_set("MOA_SPLIT_LOG2R") && !env_set("MOA_LIFT3")) {
                 lrs.clear();
                 for (int lr = std::max(1, L - 12); lr <= std::min(12, L - 1); ++lr)
                     lrs.push_back(lr);

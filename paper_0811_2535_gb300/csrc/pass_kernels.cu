@@ -28,7 +28,8 @@ template <int LOGN, bool TW4>
 __global__ void __launch_bounds__(1024) col_pass_kernel(const float2 *in, float2 *out, int C, int logF,
                                                         int logTpo, const float2 *__restrict__ tw,
                                                         const float2 *__restrict__ tw_lo,
-                                                        const float2 *__restrict__ tw_hi, int tw_h, int flags)
+                                                        const float2 *__restrict__ tw_hi, int tw_h, int flags,
+                                                        int Rt, int log_cdiv)
 {
     using Sc = Sched<LOGN>;
     extern __shared__ float2 smem[];
@@ -39,9 +40,14 @@ __global__ void __launch_bounds__(1024) col_pass_kernel(const float2 *in, float2
     const unsigned tile = blockIdx.x;
     const unsigned o = tile >> logTpo;
     const int col = (int)((tile & ((1u << logTpo) - 1)) << logF) + f;
-    // N*C < 2^31 (checked at plan time), so in-column offsets fit in 32 bits
+    // N*Rt*C < 2^31 (checked at plan time), so in-column offsets fit in 32 bits
     const int64_t base = (int64_t)o * ((int64_t)Sc::N * C) + col + (int64_t)tau * C;
     const int step = Sc::T * C;
+    // output: row k of o at row (o % Rt) + Rt*k of the [O/Rt][N*Rt][C] view
+    const unsigned ob = o / (unsigned)Rt, orow = o - ob * (unsigned)Rt;
+    const int64_t obase = (int64_t)ob * ((int64_t)Sc::N * Rt * C) + (int64_t)orow * C + col + (int64_t)tau * Rt * C;
+    const int ostep = Sc::T * Rt * C;
+    const int64_t tcol = col >> log_cdiv;   // the twiddle's column index
 
     pdl_wait_prior();   // `in` may be the previous kernel's output, `out` its input
     float2 v[16];
@@ -65,16 +71,17 @@ __global__ void __launch_bounds__(1024) col_pass_kernel(const float2 *in, float2
     float2 *tk = smem + kExchange;
     (void)tk;
     if constexpr (TW4) {
-        // w_n^(col*k1), k1 = tau + T*k, as A * Tk[k]: A = w_n^(col*tau) per
-        // thread, Tk[k] = w_n^(col*T*k) shared by the lanes of one column.
+        // w_M^(tcol*row), row = orow + Rt*(tau + T*k), as A * Tk[k]:
+        // A = w_M^(tcol*(orow + Rt*tau)) per thread, Tk[k] = w_M^(tcol*Rt*T*k)
+        // shared by the lanes of one column.
         for (int k = tau; k < Sc::P; k += Sc::T)
-            tk[(k << LAY) + f] = two_level(tw_lo, tw_hi, tw_h, (int64_t)col * (Sc::T * k));
+            tk[(k << LAY) + f] = two_level(tw_lo, tw_hi, tw_h, tcol * ((int64_t)Rt * Sc::T * k));
     }
 
     fft_tile<LOGN, LAY>(v, smem, tau, f, tw);
 
     if constexpr (TW4) {
-        const float2 A = two_level(tw_lo, tw_hi, tw_h, (int64_t)col * tau);
+        const float2 A = two_level(tw_lo, tw_hi, tw_h, tcol * (orow + (int64_t)Rt * tau));
         if constexpr (Sc::S == 1)
             __syncthreads();
 #pragma unroll
@@ -86,10 +93,10 @@ __global__ void __launch_bounds__(1024) col_pass_kernel(const float2 *in, float2
         for (int k = 0; k < Sc::P; ++k)
             v[k].y = -v[k].y;
     }
-    float2 *dst = out + base;
+    float2 *dst = out + obase;
 #pragma unroll
     for (int k = 0; k < Sc::P; ++k)
-        dst[k * step] = v[k];
+        dst[k * ostep] = v[k];
     pdl_launch_dependents();   // after the stores: the next kernel launches as the last blocks finish
 }
 
@@ -216,9 +223,15 @@ cudaError_t launch_typed(const PassDesc &d, const float2 *in, float2 *out, const
         while ((int64_t(1) << logTpo) < (d.C >> d.logF))
             ++logTpo;
         const int64_t grid = d.O << logTpo;
+        int log_cdiv = 0;
+        while ((1 << log_cdiv) < d.cdiv)
+            ++log_cdiv;
+        const bool xt = d.twlog > 0;   // a further table (a lifted axis) instead of the main one
         return launch_maybe_dependent(d.tw4 ? col_pass_kernel<LOGN, true> : col_pass_kernel<LOGN, false>,
                                       (unsigned)grid, threads, smem, stream, flags & FLAG_PDL, in, out, (int)d.C,
-                                      d.logF, logTpo, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags);
+                                      d.logF, logTpo, tw.stage[LOGN], xt ? tw.xlo[d.twlog] : tw.lo,
+                                      xt ? tw.xhi[d.twlog] : tw.hi, xt ? tw.xh[d.twlog] : tw.h, flags,
+                                      (int)(d.Rt > 1 ? d.Rt : 1), log_cdiv);
     }
     const int64_t grid = (d.O + (int64_t(1) << d.logF) - 1) >> d.logF;
     return launch_maybe_dependent(d.Rt > 1 ? row_pass_kernel<LOGN, true> : row_pass_kernel<LOGN, false>,

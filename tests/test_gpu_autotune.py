@@ -139,7 +139,8 @@ def test_every_tuned_plan_kind_matches_oracle(env, shape, batch, tmp_path, monke
     assert err.max() <= TOL
 
 
-@pytest.mark.parametrize("shape,batch,dtype", [((1 << 24,), 1, 0), ((1 << 19,), 2, 0), ((1 << 13,), 3, 0),
+@pytest.mark.parametrize("shape,batch,dtype", [((1 << 24,), 1, 0), ((1 << 25,), 1, 0), ((8192, 2048), 1, 0),
+                                               ((2048, 8192), 2, 0), ((1 << 19,), 2, 0), ((1 << 13,), 3, 0),
                                                ((1 << 10,), 4, 0), ((4096, 4096), 1, 0), ((256, 256, 256), 1, 0),
                                                ((8, 16, 32), 2, 0), ((4096,), 8, 1), ((256,), 8, 2)])
 def test_estimate_matches_the_plan(env, shape, batch, dtype, monkeypatch):

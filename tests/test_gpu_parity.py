@@ -451,3 +451,61 @@ def test_pipelined_wait_timeout_is_reported_and_contained(env, shape, monkeypatc
     plan.destroy()
     y, _ = run(env, list(shape), 1, -1, x)
     assert per_transform_rel(y, oracle_ref(env, x, list(shape), 1, -1), 1).max() <= TOL
+
+
+@pytest.mark.parametrize("shape,batch,sign", [((1 << 25,), 1, -1), ((1 << 25,), 1, 1), ((1 << 26,), 1, -1),
+                                              ((1 << 25,), 2, -1), ((8192, 2048), 1, -1), ((8192, 2048), 1, 1),
+                                              ((2048, 8192), 1, -1), ((2048, 8192), 1, 1), ((16, 8192, 8), 2, 1),
+                                              ((4, 4, 16384), 1, -1)])
+def test_long_axes_against_oracle(env, shape, batch, sign):
+    """1-D above 2^24 (three passes, n = r1*r2*c) and multi-D arrays with an
+    axis above 4096 (that axis lifted L = L1*L2 inside the array, Eq. B.6):
+    every element against the FP64 oracle."""
+    from paper_0811_2535_gb300 import inputs
+    n = 1
+    for s_ in shape:
+        n *= s_
+    x = inputs.uniform((batch,) + tuple(shape), 7500 + len(shape) + batch + (n >> 20))
+    y, info = run(env, list(shape), batch, sign, x)
+    ref = oracle_ref(env, x, list(shape), batch, sign)
+    assert per_transform_rel(y, ref, batch).max() <= TOL
+    assert info["workspace_bytes"] == 8 * n * batch
+
+
+@pytest.mark.parametrize("shape", [(1 << 25,), (8192, 2048), (2048, 8192)])
+def test_long_axes_in_place(env, shape):
+    """The first pass of a plan through the workspace keeps its tiles' places,
+    so in == out is allowed."""
+    from paper_0811_2535_gb300 import inputs
+    x = inputs.uniform(shape, 7600 + len(shape))
+    y, _ = run(env, list(shape), 1, -1, x, inplace=True)
+    assert per_transform_rel(y, oracle_ref(env, x, list(shape), 1, -1), 1).max() <= TOL
+
+
+def test_1d_2_28_closed_forms(env):
+    """n = 2^28, where the oracle would take minutes: a shifted delta gives
+    X[k] = w_n^(j0*k) (checked on 4096 sampled bins, exponent reduced exactly
+    mod n in int64, FP64 reference), and Parseval holds on a random input."""
+    torch, moafft, _ = env
+    n = 1 << 28
+    plan = moafft.Plan([n], 1, -1)
+    assert plan.info()["passes"] == 3
+    x = torch.zeros(n, dtype=torch.complex64, device="cuda")
+    j0 = 123456789
+    x[j0] = 1.0
+    y = plan.exec(x)
+    rng = np.random.default_rng(8)
+    k = np.sort(rng.choice(n, 4096, replace=False)).astype(np.int64)
+    got = y[torch.from_numpy(k).cuda()].cpu().numpy().astype(np.complex128)
+    e = (j0 * k) % n
+    ref = np.exp(-2j * np.pi * (e.astype(np.float64) / n))
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= TOL
+    g = torch.Generator(device="cuda").manual_seed(9)
+    xr = torch.complex(torch.rand(n, device="cuda", generator=g) * 2 - 1,
+                       torch.rand(n, device="cuda", generator=g) * 2 - 1)
+    yr = plan.exec(xr)
+    assert plan.status() == 0
+    ex = (xr.abs().double() ** 2).sum().item() * n
+    ey = (yr.abs().double() ** 2).sum().item()
+    assert abs(ey - ex) / ex <= 1e-6
+    plan.destroy()

@@ -105,7 +105,8 @@ def test_estimate_rejects_what_plan_rejects(mf):
 
     assert code([1 << 24]) == 0
     assert code([12]) == 2 and code([1]) == 2 and code([8, 6]) == 2        # not a power of two >= 2
-    assert code([1 << 25]) == 3 and code([8192, 2]) == 3                  # beyond the supported sizes
+    assert code([1 << 25]) == 0 and code([8192, 2]) == 0                  # lifted further / a long axis
+    assert code([1 << 31]) == 3 and code([1 << 25, 2]) == 3               # beyond the supported sizes
     assert code([1 << 24], batch=128) == 3                                # 2^31 elements
     assert code([64], dtype=1) == 3                                       # tensor cores: 256 or 4096 only
     assert code([8], batch=0) == 1 and code([8], dtype=7) == 1 and code([2, 2, 2, 2]) == 1
@@ -116,3 +117,42 @@ def test_estimate_rejects_what_plan_rejects(mf):
     assert code([1 << 24], buf=small, buflen=8) == 0 and small.value == b"pipe_co"
     with pytest.raises(mf.MoaError):
         mf.estimate([3])
+
+
+@pytest.mark.parametrize("L", range(25, 31))
+@pytest.mark.parametrize("tma", [TMA, NO_TMA])
+def test_1d_beyond_2_24(mf, L, tma):
+    """n > 2^24: n = r1*r2*c (Sec. 4.2 applied twice; c = 2^ceil(L/3), r = r1*r2
+    balanced): an r2-point column pass with the twiddle of the r-point
+    transform, an r1-point column pass storing row k1s + r2*k1f with the
+    four-step twiddle, then the c-point rows stored transposed; in -> out ->
+    workspace -> out."""
+    e = mf.estimate([1 << L], 1, tma=tma)
+    lc = (L + 2) // 3
+    lr = L - lc
+    lr1, lr2 = (lr + 1) // 2, lr - (lr + 1) // 2
+    assert (e["passes"], e["split_r"], e["split_c"], e["workspace_bytes"]) == (3, 1 << lr, 1 << lc, 8 << L)
+    row = f"pipe_rowT_kernel<{lc}>" if tma == TMA and lc >= 10 else f"row_pass_kernel<{lc},1>"
+    assert e["kernels"] == [f"col_pass_kernel<{lr2},1>", f"col_pass_kernel<{lr1},1>", row]
+
+
+@pytest.mark.parametrize("shape,batch,kernels", [
+    ((8192, 2048), 1, ["row_pass_kernel<11,0>", "col_pass_kernel<6,1>", "col_pass_kernel<7,0>"]),
+    ((2048, 8192), 1, ["col_pass_kernel<6,1>", "row_pass_kernel<7,1>", "pipe_col_kernel<11,0,0>"]),
+    ((16, 8192, 8), 2, ["row_pass_kernel<3,0>", "col_pass_kernel<6,1>", "col_pass_kernel<7,0>",
+                        "col_pass_kernel<4,0>"]),
+    ((1 << 20, 2), 1, ["row_pass_kernel<1,0>", "col_pass_kernel<10,1>", "col_pass_kernel<10,0>"]),
+    ((8192, 8192), 1, ["col_pass_kernel<6,1>", "row_pass_kernel<7,1>", "col_pass_kernel<6,1>",
+                       "col_pass_kernel<7,0>"])])
+def test_multi_d_long_axes(mf, shape, batch, kernels):
+    """Eq. B.6 with an axis longer than 4096: that axis lifted L = L1*L2
+    (L2 = 2^floor(l/2) points over the slow half with the twiddle, then L1
+    points over the fast half, the last axis's second half as a transposed
+    row pass), the other axes one pass each; every pass through the
+    workspace, the last into the output."""
+    e = mf.estimate(list(shape), batch, tma=TMA)
+    n = batch
+    for s_ in shape:
+        n *= s_
+    assert e["kernels"] == kernels
+    assert (e["passes"], e["workspace_bytes"]) == (len(kernels), 8 * n)
