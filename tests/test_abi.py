@@ -73,8 +73,8 @@ def test_invalid_args_rejected_on_host(L):
 
 
 def test_unsupported_requests(L):
-    assert _plan(L, [1 << 25])[0] == 3                 # 1-D beyond 2^24
-    assert _plan(L, [8192, 2])[0] == 3                 # multi-D axis beyond 4096
+    assert _plan(L, [1 << 31])[0] == 3                 # 1-D beyond 2^30
+    assert _plan(L, [1 << 25, 2])[0] == 3              # multi-D axis beyond 2^24
     assert _plan(L, [1 << 24], batch=128)[0] == 3      # more than 2^31 elements
     assert _plan(L, [8], dtype=1)[0] == 3              # tensor-core path: n = 256 or 4096 only
     assert _plan(L, [64, 64], dtype=2)[0] == 3
