@@ -11,9 +11,10 @@
 // each block is persistent and refills its shared memory asynchronously:
 //
 //   H (landing buffer): TMA brings the first part of tile i+1 while tile i
-//     computes: for columns, as many 256-row boxes (cp.async.bulk.tensor,
-//     256 rows x 32 bytes) as fit beside E, 11 of 16 at N = 4096; for rows,
-//     the first half of each row (cp.async.bulk);
+//     computes: for columns, as many 256-row boxes (256 rows x 32 bytes) as
+//     fit beside E, 11 of 16 at N = 4096, in one cp.async.bulk.tensor copy
+//     whose box spans those 256-row blocks; for rows, the first half of each
+//     row (cp.async.bulk);
 //   E (exchange buffer, (N + N/16) x 4 complex64): the single-round register
 //     exchanges of tile i's radix-16 stages; as soon as the last exchange has
 //     been read, TMA lands the rest of tile i+1 in it, overlapping the last
@@ -64,21 +65,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(smem_u32(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z)
 {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
         "[%5];" ::"r"(smem_u32(dst)),
         "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z,
+                                            int w)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
         : "memory");
 }
 
@@ -254,7 +256,8 @@ __device__ __forceinline__ void three_stages(float2 (&v)[16], float2 *E, int tau
 // exchange, which one thread waits for at the tile start.
 template <int LOGN, bool TW4, int BLK>
 __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
-    pipe_col_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap, float2 *out,
+    pipe_col_kernel(const __grid_constant__ CUtensorMap tmapH, const __grid_constant__ CUtensorMap tmapE,
+                    const __grid_constant__ CUtensorMap omap, float2 *out,
                     int C, int logTpo, int ntiles, const float2 *__restrict__ tw, const float2 *__restrict__ tw_lo,
                     const float2 *__restrict__ tw_hi, int tw_h, int flags, int staged, int *status)
 {
@@ -274,19 +277,21 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
 
     // rows [0, HR) (h = 0) or [HR, N) (h = 1) of the tile's four columns, as
     // boxes of 256 rows x 32 bytes
+    // rows [0, HR) (h = 0) or [HR, N) (h = 1) of the tile's four columns: one
+    // TMA copy of HR / 256 (or (N - HR) / 256) boxes of 256 rows x 32 bytes,
+    // through the tensor map of that depth
     auto issue_half = [&](int tile, int h, float2 *dst, uint64_t *b) {
         const int o = tile >> logTpo;
         const int c0 = (tile & tpo_mask) << 2;
         const int r0 = h ? HR : 0, nb = (h ? N - HR : HR) / 256;
+        const CUtensorMap *map = h ? &tmapE : &tmapH;
         mbar_arrive_expect_tx(b, nb * 256 * 4 * (uint32_t)sizeof(float2));
-        for (int k = 0; k < nb; ++k) {
-            if constexpr (BLK == 3)
-                tma_load_3d(dst + k * 256 * 4, &tmap, b, 2 * (c0 & 255), o * 256, 16 * (c0 >> 8) + (r0 >> 8) + k);
-            else if constexpr (BLK == 2)
-                tma_load_3d(dst + k * 256 * 4, &tmap, b, 0, c0 >> 2, (o * N + r0 + k * 256) >> 2);
-            else
-                tma_load_2d(dst + k * 256 * 4, &tmap, b, 2 * c0, o * N + r0 + k * 256);
-        }
+        if constexpr (BLK == 3)
+            tma_load_3d(dst, map, b, 2 * (c0 & 255), o * 256, 16 * (c0 >> 8) + (r0 >> 8));
+        else if constexpr (BLK == 2)
+            tma_load_4d(dst, map, b, 0, c0 >> 2, 0, (o * N + r0) >> 8);
+        else
+            tma_load_3d(dst, map, b, 2 * c0, 0, (o * N + r0) >> 8);
     };
 
     if (tid == 0) {
@@ -626,26 +631,35 @@ cudaError_t launch_col(const PassDesc &d, int64_t O, int64_t C, int blk, const f
     EncodeTiledFn enc = encode_fn();
     if (!enc)
         return cudaErrorNotSupported;
-    CUtensorMap map;
-    CUresult r;
-    if (blk == 2) {
-        // {floats of one 4 x 4 block, blocks along k1, blocks along j2 of every o}
-        const cuuint64_t dims[3] = {32, (cuuint64_t)(C >> 2), (cuuint64_t)(O << (LOGN - 2))};
-        const cuuint64_t strides[2] = {128, (cuuint64_t)((C >> 2) * 128)};
-        const cuuint32_t box[3] = {32, 1, 64};
-        const cuuint32_t estr[3] = {1, 1, 1};
-        r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2 *>(in), dims, strides, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    } else {
-        const cuuint64_t dims[2] = {(cuuint64_t)(2 * C), (cuuint64_t)(O << LOGN)};
-        const cuuint64_t strides[1] = {(cuuint64_t)(2 * C * sizeof(float))};
-        const cuuint32_t box[2] = {8, 256};
-        const cuuint32_t estr[2] = {1, 1};
-        r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2 *>(in), dims, strides, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    // the tile's first HR rows (early landing) and the rest, each one TMA copy
+    // of whole 256-row boxes: depth HR/256 and (N - HR)/256 along a dimension
+    // of 256-row blocks
+    constexpr int HR = PipeSmem::early_rows<LOGN>();
+    const cuuint32_t depth[2] = {(cuuint32_t)(HR / 256), (cuuint32_t)(((1 << LOGN) - HR) / 256)};
+    CUtensorMap maps[2];
+    CUresult r = CUDA_SUCCESS;
+    for (int h = 0; h < 2 && r == CUDA_SUCCESS; ++h) {
+        if (blk == 2) {
+            // {floats of one 4 x 4 block, blocks along k1, 64 blocks along j2, 256-row blocks of every o}
+            const cuuint64_t dims[4] = {32, (cuuint64_t)(C >> 2), 64, (cuuint64_t)((O << LOGN) >> 8)};
+            const cuuint64_t strides[3] = {128, (cuuint64_t)((C >> 2) * 128), (cuuint64_t)(64 * (C >> 2) * 128)};
+            const cuuint32_t box[4] = {32, 1, 64, depth[h]};
+            const cuuint32_t estr[4] = {1, 1, 1, 1};
+            r = enc(&maps[h], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float2 *>(in), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        } else {
+            // {floats of a row, rows of a 256-row block, 256-row blocks of every o}
+            const cuuint64_t dims[3] = {(cuuint64_t)(2 * C), 256, (cuuint64_t)((O << LOGN) >> 8)};
+            const cuuint64_t strides[2] = {(cuuint64_t)(2 * C * sizeof(float)), (cuuint64_t)(256 * 2 * C * sizeof(float))};
+            const cuuint32_t box[3] = {8, 256, depth[h]};
+            const cuuint32_t estr[3] = {1, 1, 1};
+            r = enc(&maps[h], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2 *>(in), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        }
     }
+    const CUtensorMap &map = maps[0];
     if (r != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     int logTpo = 0;
@@ -665,8 +679,8 @@ cudaError_t launch_col(const PassDesc &d, int64_t O, int64_t C, int blk, const f
     auto kern = blk == 2 ? pipe_col_kernel<LOGN, false, 2>
                          : (d.tw4 && blk == 1 ? pipe_col_kernel<LOGN, true, 1>
                                               : (d.tw4 ? pipe_col_kernel<LOGN, true, 0> : pipe_col_kernel<LOGN, false, 0>));
-    return launch_maybe_dependent(kern, grid, 1 << (LOGN - 2), smem, stream, flags & FLAG_PDL, map, omap, out, Ci,
-                                  logTpo, ntiles, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags, staged, status);
+    return launch_maybe_dependent(kern, grid, 1 << (LOGN - 2), smem, stream, flags & FLAG_PDL, maps[0], maps[1], omap,
+                                  out, Ci, logTpo, ntiles, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags, staged, status);
 }
 
 // Second pass of the two-pass 3-D transform of O arrays of 256^3 (BLK = 3).
@@ -676,16 +690,21 @@ cudaError_t launch_plane2(int64_t O, const float2 *in, float2 *out, const Twiddl
     EncodeTiledFn enc = encode_fn();
     if (!enc)
         return cudaErrorNotSupported;
-    CUtensorMap map;
-    // {floats of one row, planes of all O arrays, rows of a plane}
-    const cuuint64_t dims[3] = {512, (cuuint64_t)(O * 256), 256};
-    const cuuint64_t strides[2] = {(cuuint64_t)65536 * sizeof(float2), (cuuint64_t)256 * sizeof(float2)};
-    const cuuint32_t box[3] = {8, 256, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2 *>(in), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
+    // {floats of one row, planes of all O arrays, rows of a plane}; the early
+    // and the late part of a tile as one copy each (boxes of 11 and 5 rows)
+    constexpr int HR = PipeSmem::early_rows<12>();
+    CUtensorMap maps[2];
+    for (int h = 0; h < 2; ++h) {
+        const cuuint64_t dims[3] = {512, (cuuint64_t)(O * 256), 256};
+        const cuuint64_t strides[2] = {(cuuint64_t)65536 * sizeof(float2), (cuuint64_t)256 * sizeof(float2)};
+        const cuuint32_t box[3] = {8, 256, (cuuint32_t)(h ? (4096 - HR) / 256 : HR / 256)};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        if (enc(&maps[h], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2 *>(in), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    const CUtensorMap &map = maps[0];
     const int ntiles = (int)(O << 10);   // 16 row groups x 64 column groups per array
     const int nsm = num_sms_current();
     const int grid = ntiles < nsm ? ntiles : nsm;
@@ -704,8 +723,8 @@ cudaError_t launch_plane2(int64_t O, const float2 *in, float2 *out, const Twiddl
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     }
     return launch_maybe_dependent(pipe_col_kernel<12, false, 3>, grid, 1024, col_smem<12>(), stream, flags & FLAG_PDL,
-                                  map, omap, out, 256, 10, ntiles, tw.stage[12], tw.lo, tw.hi, tw.h, flags, staged,
-                                  status);
+                                  maps[0], maps[1], omap, out, 256, 10, ntiles, tw.stage[12], tw.lo, tw.hi, tw.h,
+                                  flags, staged, status);
 }
 
 template <int LOGN>
