@@ -83,6 +83,9 @@ cudaError_t launch_pass(const PassDesc &d, const float2 *in, float2 *out, const 
 // usable when the driver exposes cuTensorMapEncodeTiled.  The input must be
 // 16-byte aligned.
 bool pipe_supported();
+// whether the pipelined column passes of N = 4096 run two columns per thread
+// (pipe_col2_kernel; MOA_COL2=0 selects the four-column pipe_col_kernel)
+bool pipe_col2_active();
 // Tiled TMA tensor map of 8-byte elements (complex64 moved as 64-bit words):
 // dims / box in elements, innermost first; strides in bytes of dims 1..rank-1.
 bool encode_c64_map(CUtensorMap *map, const void *base, int rank, const uint64_t *dims, const uint64_t *strides,

@@ -1087,8 +1087,12 @@ void pass_name(const moa_fft_plan_s *p, const PassDesc &d, char *buf, size_t len
         snprintf(buf, len, "lift3_kernel<%d,%d>", d.logF, d.logN);
     else if (d.kind == moa::PASS_PLANE1)
         snprintf(buf, len, "plane3d_p1_kernel");
+    // N = 4096 column passes run two columns per thread (four with MOA_COL2=0,
+    // or on an output that is only 8-byte aligned)
     else if (d.kind == moa::PASS_PLANE2)
-        snprintf(buf, len, "pipe_col_kernel<12,0,3>");
+        snprintf(buf, len, moa::pipe_col2_active() ? "pipe_col2_kernel<0,3>" : "pipe_col_kernel<12,0,3>");
+    else if (d.pipe && (d.kind == moa::PASS_COL || d.blk == 2) && d.logN == 12 && moa::pipe_col2_active())
+        snprintf(buf, len, "pipe_col2_kernel<%d,%d>", d.tw4, d.blk);
     else if (d.pipe && (d.kind == moa::PASS_COL || d.blk == 2))
         snprintf(buf, len, "pipe_col_kernel<%d,%d,%d>", d.logN, d.tw4, d.blk);
     else if (d.pipe)

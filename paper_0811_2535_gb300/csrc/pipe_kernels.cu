@@ -198,6 +198,28 @@ __device__ __forceinline__ void drain_in_flight(uint64_t *bar, uint32_t parity)
         }
 }
 
+// Rows [0, HR) (h = 0) or [HR, N) (h = 1) of a column tile's four columns:
+// one TMA copy of HR / 256 (or (N - HR) / 256) boxes of 256 rows x 32 bytes,
+// through the tensor map of that depth (tmapH for h = 0, tmapE for h = 1).
+template <int LOGN, int BLK>
+__device__ __forceinline__ void issue_tile_part(const CUtensorMap *tmapH, const CUtensorMap *tmapE, int logTpo,
+                                                int tile, int h, float2 *dst, uint64_t *b)
+{
+    constexpr int N = 1 << LOGN;
+    constexpr int HR = PipeSmem::early_rows<LOGN>();
+    const int o = tile >> logTpo;
+    const int c0 = (tile & ((1 << logTpo) - 1)) << 2;
+    const int r0 = h ? HR : 0, nb = (h ? N - HR : HR) / 256;
+    const CUtensorMap *map = h ? tmapE : tmapH;
+    mbar_arrive_expect_tx(b, nb * 256 * 4 * (uint32_t)sizeof(float2));
+    if constexpr (BLK == 3)
+        tma_load_3d(dst, map, b, 2 * (c0 & 255), o * 256, 16 * (c0 >> 8) + (r0 >> 8));
+    else if constexpr (BLK == 2)
+        tma_load_4d(dst, map, b, 0, c0 >> 2, 0, (o * N + r0) >> 8);
+    else
+        tma_load_3d(dst, map, b, 2 * c0, 0, (o * N + r0) >> 8);
+}
+
 // The three radix stages of N = 1024, 2048, 4096 (radix 4/8/16, 16, 16) with
 // single-round exchanges through E; `after_last_read` runs once E is no
 // longer needed (used to start refilling it).
@@ -275,23 +297,8 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
     const int f = tid & 3, tau = tid >> 2;
     const unsigned tpo_mask = (1u << logTpo) - 1;
 
-    // rows [0, HR) (h = 0) or [HR, N) (h = 1) of the tile's four columns, as
-    // boxes of 256 rows x 32 bytes
-    // rows [0, HR) (h = 0) or [HR, N) (h = 1) of the tile's four columns: one
-    // TMA copy of HR / 256 (or (N - HR) / 256) boxes of 256 rows x 32 bytes,
-    // through the tensor map of that depth
     auto issue_half = [&](int tile, int h, float2 *dst, uint64_t *b) {
-        const int o = tile >> logTpo;
-        const int c0 = (tile & tpo_mask) << 2;
-        const int r0 = h ? HR : 0, nb = (h ? N - HR : HR) / 256;
-        const CUtensorMap *map = h ? &tmapE : &tmapH;
-        mbar_arrive_expect_tx(b, nb * 256 * 4 * (uint32_t)sizeof(float2));
-        if constexpr (BLK == 3)
-            tma_load_3d(dst, map, b, 2 * (c0 & 255), o * 256, 16 * (c0 >> 8) + (r0 >> 8));
-        else if constexpr (BLK == 2)
-            tma_load_4d(dst, map, b, 0, c0 >> 2, 0, (o * N + r0) >> 8);
-        else
-            tma_load_3d(dst, map, b, 2 * c0, 0, (o * N + r0) >> 8);
+        issue_tile_part<LOGN, BLK>(&tmapH, &tmapE, logTpo, tile, h, dst, b);
     };
 
     if (tid == 0) {
@@ -436,6 +443,293 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
         }
     }
     if (LOGN == 12 && staged && tid == 0)
+        bulk_wait_all();   // the staged stores are complete before the block exits
+}
+
+// ---------------------------------------------------------------------------
+// Two columns per thread (N = 4096).  The four columns of a tile are four
+// independent transforms with the same butterflies and the same stage
+// twiddles, so a thread can carry two of them: 512 threads, thread (tau, g)
+// holds columns 2g and 2g+1 in v and u.  The shared-memory layouts stay those
+// of the four-column kernel (element e of column f at byte 32*pad16(e) + 8f),
+// in which the two columns of a thread are 16 contiguous bytes: every
+// landing, exchange and staging access moves a float4, half the shared-memory
+// instructions; the stage twiddle rows are loaded and their products formed
+// once for both columns.  The arithmetic of each column is that of the
+// four-column kernel, operation for operation.
+
+// Stage s of the three radix-16 stages on the two transforms of a thread;
+// TWID = false leaves out the stage twiddles (as stage_compute does).
+template <int s, bool TWID = true>
+__device__ __forceinline__ void stage_compute2(float2 (&v)[16], float2 (&u)[16], int tau,
+                                               const float2 *__restrict__ tw)
+{
+    using Sc = Sched<12>;
+    dft16(v);
+    dft16(u);
+    if constexpr (TWID && s != Sc::S - 1) {
+        // twiddle w_M^(uu*k) on output k: rows k = 1, 2, 3, 4, 8, 12 of the
+        // stage table, the others as products (the rows and products of
+        // apply_twiddles<16>)
+        constexpr int M1 = Sc::M1(s);
+        const float2 *t = tw + Sc::tw_offset(s);
+        const int uu = tau & (M1 - 1);
+        const float2 w1 = __ldg(&t[uu]), w2 = __ldg(&t[M1 + uu]), w3 = __ldg(&t[2 * M1 + uu]);
+        v[1] = cmul(v[1], w1);
+        u[1] = cmul(u[1], w1);
+        v[2] = cmul(v[2], w2);
+        u[2] = cmul(u[2], w2);
+        v[3] = cmul(v[3], w3);
+        u[3] = cmul(u[3], w3);
+#pragma unroll
+        for (int j = 1; j < 4; ++j) {
+            const float2 wj = __ldg(&t[(j + 2) * M1 + uu]);   // k = 4, 8, 12
+            const float2 a = cmul(wj, w1), b = cmul(wj, w2), c = cmul(wj, w3);
+            v[4 * j] = cmul(v[4 * j], wj);
+            u[4 * j] = cmul(u[4 * j], wj);
+            v[4 * j + 1] = cmul(v[4 * j + 1], a);
+            u[4 * j + 1] = cmul(u[4 * j + 1], a);
+            v[4 * j + 2] = cmul(v[4 * j + 2], b);
+            u[4 * j + 2] = cmul(u[4 * j + 2], b);
+            v[4 * j + 3] = cmul(v[4 * j + 3], c);
+            u[4 * j + 3] = cmul(u[4 * j + 3], c);
+        }
+    }
+}
+
+// Stage s outputs e = tau + 256k of both columns to the exchange buffer.
+template <int s>
+__device__ __forceinline__ void stage_write2(const float2 (&v)[16], const float2 (&u)[16], float4 *sm, int tau, int g)
+{
+    using Sc = Sched<12>;
+    constexpr int KM1 = Sc::K(s) * Sc::M1(s);   // 256
+    float4 *p = sm + (pad16(tau) << 1) + g;
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+        p[pad16(KM1 * k) << 1] = make_float4(v[k].x, v[k].y, u[k].x, u[k].y);
+}
+
+// Stage s inputs e = w + M1*m of both columns from the exchange buffer.
+template <int s>
+__device__ __forceinline__ void stage_read2(float2 (&v)[16], float2 (&u)[16], const float4 *sm, int tau, int g)
+{
+    using Sc = Sched<12>;
+    constexpr int M1 = Sc::M1(s), M = M1 * 16;
+    const int w = (tau / M1) * M + (tau & (M1 - 1));
+    const float4 *p = sm + (pad16(w) << 1) + g;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        const float4 a = p[pad16(M1 * m) << 1];
+        v[m] = make_float2(a.x, a.y);
+        u[m] = make_float2(a.z, a.w);
+    }
+}
+
+// BLK as in pipe_col_kernel; N = 4096, 512 threads.  The output must be
+// 16-byte aligned (the plain stores write both columns as one float4).
+template <bool TW4, int BLK>
+__global__ void __launch_bounds__(512, 1)
+    pipe_col2_kernel(const __grid_constant__ CUtensorMap tmapH, const __grid_constant__ CUtensorMap tmapE,
+                     const __grid_constant__ CUtensorMap omap, float2 *out, int C, int logTpo, int ntiles,
+                     const float2 *__restrict__ tw, const float2 *__restrict__ tw_lo,
+                     const float2 *__restrict__ tw_hi, int tw_h, int flags, int staged, int *status)
+{
+    constexpr int N = 4096, T = 256;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    float2 *E = reinterpret_cast<float2 *>(smem_raw);
+    float2 *H = E + PipeSmem::E_entries<12>();
+    constexpr int HR = PipeSmem::early_rows<12>();   // rows landing in H; rows HR..N-1 land in E
+    float2 *tk = H + 4 * HR;                         // [16][4] four-step twiddle factors
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tk + 64);
+    int *abort_flag = reinterpret_cast<int *>(bar + 2);
+    float4 *E4 = reinterpret_cast<float4 *>(E);
+    const float4 *H4 = reinterpret_cast<const float4 *>(H);
+
+    const int tid = threadIdx.x;
+    const int g = tid & 1, tau = tid >> 1;
+    const unsigned tpo_mask = (1u << logTpo) - 1;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        *abort_flag = 0;
+    }
+    __syncthreads();
+    int tile = blockIdx.x;
+    if (tid == 0 && tile < ntiles) {
+        pdl_wait_prior();   // the input may be the previous kernel's output
+        issue_tile_part<12, BLK>(&tmapH, &tmapE, logTpo, tile, 0, H, &bar[0]);
+        issue_tile_part<12, BLK>(&tmapH, &tmapE, logTpo, tile, 1, E, &bar[1]);
+    }
+    uint32_t parity = 0;
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int o = tile >> logTpo;
+        const int c0 = (tile & tpo_mask) << 2;
+        const int col = c0 + 2 * g;   // the thread's first column; the second is col + 1
+        const int next = tile + (int)gridDim.x;
+        if (next >= ntiles)
+            pdl_launch_dependents();   // the block's last tile: let the next kernel launch
+        if (tid == 0) {
+            bounded_wait(&bar[0], parity, status, abort_flag, flags);
+            bounded_wait(&bar[1], parity, status, abort_flag, flags);
+            if (*abort_flag)
+                drain_in_flight(bar, parity);
+        }
+        __syncthreads();
+        if (*abort_flag) {
+            if (staged && tid == 0)
+                bulk_wait_all();   // no staged store may still read E
+            return;
+        }
+        parity ^= 1u;
+
+        // element tau + T*q of both columns (rows below HR in H, the others in E)
+        float2 v[16], u[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const float4 a = q * T < HR ? H4[(tau + T * q) * 2 + g] : E4[(tau + T * q - HR) * 2 + g];
+            v[q] = make_float2(a.x, a.y);
+            u[q] = make_float2(a.z, a.w);
+        }
+        if (staged && tid == 0)
+            bulk_wait_read();   // the previous tile's staged outputs have left E
+        __syncthreads();   // H and E have been read
+        if (tid == 0 && next < ntiles) {
+            fence_proxy_async();
+            issue_tile_part<12, BLK>(&tmapH, &tmapE, logTpo, next, 0, H, &bar[0]);
+        }
+        if (flags & FLAG_CONJ_IN) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                v[r].y = -v[r].y;
+                u[r].y = -u[r].y;
+            }
+        }
+        if constexpr (TW4) {
+            // tk[k][f] = w^(column f * T*k), 64 entries, one per thread of the first 64
+            if (tid < 64)
+                tk[tid] = two_level_tw(tw_lo, tw_hi, tw_h, (int64_t)(c0 + (tid & 3)) * (T * (tid >> 2)));
+        }
+
+        stage_compute2<0, BLK != 3>(v, u, tau, tw);
+        stage_write2<0>(v, u, E4, tau, g);
+        __syncthreads();
+        stage_read2<1>(v, u, E4, tau, g);
+        __syncthreads();
+        stage_compute2<1>(v, u, tau, tw);
+        stage_write2<1>(v, u, E4, tau, g);
+        __syncthreads();
+        stage_read2<2>(v, u, E4, tau, g);
+        __syncthreads();
+        if (tid == 0 && next < ntiles) {
+            fence_proxy_async();
+            issue_tile_part<12, BLK>(&tmapH, &tmapE, logTpo, next, 1, E, &bar[1]);
+        }
+        stage_compute2<2>(v, u, tau, tw);
+
+        if constexpr (TW4) {
+            // w^(col * (tau + T*k)) = A * tk[k][col]
+            const float2 A0 = two_level_tw(tw_lo, tw_hi, tw_h, (int64_t)col * tau);
+            const float2 A1 = two_level_tw(tw_lo, tw_hi, tw_h, (int64_t)(col + 1) * tau);
+            const float4 *tk4 = reinterpret_cast<const float4 *>(tk);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const float4 t = tk4[k * 2 + g];
+                v[k] = cmul(v[k], cmul(A0, make_float2(t.x, t.y)));
+                u[k] = cmul(u[k], cmul(A1, make_float2(t.z, t.w)));
+            }
+        }
+        if (flags & FLAG_CONJ_OUT) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                v[k].y = -v[k].y;
+                u[k].y = -u[k].y;
+            }
+        }
+        // outputs k >= k0 of the thread with plain stores
+        auto store_plain = [&](int k0) {
+            if constexpr (BLK == 3) {
+                // output k = k1a + 16*k0 with tau + T*k = k: k1a = tau % 16, k0 = tau/16 + 16*k
+                float4 *dst = reinterpret_cast<float4 *>(out + ((int64_t)o << 24) + (int64_t)(tau >> 4) * 65536 +
+                                                         ((col >> 8) + 16 * (tau & 15)) * 256 + (col & 255));
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (k >= k0)
+                        dst[(int64_t)k << 19] = make_float4(v[k].x, v[k].y, u[k].x, u[k].y);
+            } else if constexpr (BLK == 1) {
+                // element (tau + T*k, col) of the tile: block ((col/4)*(N/4) + (tau + T*k)/4),
+                // slot (col%4)*4 + tau%4; the second column is 4 slots on
+                float2 *dst = out + (int64_t)o * N * C + (int64_t)((col >> 2) * (N >> 2)) * 16 + (col & 3) * 4 +
+                              (tau >> 2) * 16 + (tau & 3);
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (k >= k0) {
+                        dst[k * 4 * T] = v[k];
+                        dst[k * 4 * T + 4] = u[k];
+                    }
+            } else {
+                float4 *dst = reinterpret_cast<float4 *>(out + (int64_t)o * N * C + col + (int64_t)tau * C);
+                const int64_t step = (int64_t)T * C / 2;
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (k >= k0)
+                        dst[k * step] = make_float4(v[k].x, v[k].y, u[k].x, u[k].y);
+            }
+        };
+        if (staged) {
+            // slices 0..KS-1 to E behind the late rows of the next tile, the rest plain
+            constexpr int LATE = N - HR;
+            constexpr int KS = (PipeSmem::E_entries<12>() - 4 * LATE) / (4 * T);
+            static_assert(KS >= 1 && KS < 16 && (4 * LATE * 8) % 1024 == 0, "staging slices");
+            float2 *stg = E + 4 * LATE;
+            if constexpr (BLK == 1) {
+                // slot (col%4)*4 + tau%4 of block (tau/4 + 64k), stored with the
+                // 128-byte swizzle of the output tensor map (16-byte chunk j of
+                // block b at chunk j ^ (b % 8)), so that the blocks of a warp's
+                // four tau groups fall on different banks; b % 8 = (tau/4) % 8
+                char *sb = reinterpret_cast<char *>(stg) + (tau >> 2) * 128 + (tau & 1) * 8;
+                const int sw = (tau >> 2) & 7, ch = 4 * g + ((tau >> 1) & 1);   // chunk of the first column
+                float2 *p0 = reinterpret_cast<float2 *>(sb + ((ch ^ sw) << 4));
+                float2 *p1 = reinterpret_cast<float2 *>(sb + (((ch + 2) ^ sw) << 4));
+#pragma unroll
+                for (int k = 0; k < KS; ++k) {
+                    p0[k * 4 * T] = v[k];
+                    p1[k * 4 * T] = u[k];
+                }
+            } else {
+                float4 *sp = reinterpret_cast<float4 *>(stg) + tau * 2 + g;
+#pragma unroll
+                for (int k = 0; k < KS; ++k)
+                    sp[k * 2 * T] = make_float4(v[k].x, v[k].y, u[k].x, u[k].y);
+            }
+            store_plain(KS);
+            __syncthreads();   // the staged slices are complete
+            if (tid == 0) {
+                fence_proxy_async();   // written through the generic proxy, read by TMA
+                if constexpr (BLK == 1) {
+                    // three boxes of 256 blocks (32 KiB) of the map over the blocked output
+                    static_assert(KS * 64 == 3 * 256, "three boxes of 256 blocks");
+                    const int b0 = o * (N / 16) * C + (c0 >> 2) * (N >> 2);
+#pragma unroll 1
+                    for (int j = 0; j < 3; ++j)
+                        tma_store_2d(&omap, stg + j * 256 * 16, 0, b0 + 256 * j);
+                } else {
+#pragma unroll 1
+                    for (int k = 0; k < KS; ++k) {
+                        if constexpr (BLK == 3)
+                            tma_store_4d(&omap, stg + k * 4 * T, 2 * (c0 & 255), c0 >> 8, 0, o * 256 + 16 * k);
+                        else
+                            tma_store_2d(&omap, stg + k * 4 * T, 2 * c0, o * N + T * k);
+                    }
+                }
+                bulk_commit();
+            }
+        } else {
+            store_plain(0);
+        }
+    }
+    if (staged && tid == 0)
         bulk_wait_all();   // the staged stores are complete before the block exits
 }
 
@@ -605,6 +899,16 @@ bool staged_enabled()
     return on;
 }
 
+// Two columns per thread at N = 4096 (MOA_COL2=0: the four-column kernel).
+bool col2_enabled()
+{
+    static const bool on = [] {
+        const char *s = std::getenv("MOA_COL2");
+        return !(s && *s && std::atoi(s) == 0);
+    }();
+    return on;
+}
+
 // Output tensor map of the staged stores over the [O][N][C] view: {2C floats,
 // O*N rows}, boxes of 4 columns x 256 rows.  False when the output cannot be
 // a TMA target (not 16-byte aligned).
@@ -619,6 +923,23 @@ bool encode_out_rows(CUtensorMap *map, float2 *out, int64_t O, int64_t C, int lo
     const cuuint32_t estr[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, out, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Output tensor map of the two-column kernel's staged blocked stores: the
+// blocked workspace as {32 floats (one 4 x 4 block), blocks}, boxes of 256
+// blocks, 128-byte swizzle.  False when it cannot be encoded.
+bool encode_out_blocked(CUtensorMap *map, float2 *out, int64_t nblocks)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc || (reinterpret_cast<uintptr_t>(out) & 15) != 0)
+        return false;
+    const cuuint64_t dims[2] = {32, (cuuint64_t)nblocks};
+    const cuuint64_t strides[1] = {128};
+    const cuuint32_t box[2] = {32, 256};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, out, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -676,6 +997,15 @@ cudaError_t launch_col(const PassDesc &d, int64_t O, int64_t C, int blk, const f
     int staged = 0;
     if (LOGN == 12 && staged_enabled())
         staged = blk == 1 ? (reinterpret_cast<uintptr_t>(out) & 15) == 0 : encode_out_rows(&omap, out, O, C, LOGN);
+    if (LOGN == 12 && col2_enabled() && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+        if (blk == 1 && staged)
+            staged = encode_out_blocked(&omap, out, (O << LOGN) * C / 16);
+        auto kern2 = blk == 2 ? pipe_col2_kernel<false, 2>
+                              : (d.tw4 && blk == 1 ? pipe_col2_kernel<true, 1>
+                                                   : (d.tw4 ? pipe_col2_kernel<true, 0> : pipe_col2_kernel<false, 0>));
+        return launch_maybe_dependent(kern2, grid, 512, smem, stream, flags & FLAG_PDL, maps[0], maps[1], omap, out,
+                                      Ci, logTpo, ntiles, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags, staged, status);
+    }
     auto kern = blk == 2 ? pipe_col_kernel<LOGN, false, 2>
                          : (d.tw4 && blk == 1 ? pipe_col_kernel<LOGN, true, 1>
                                               : (d.tw4 ? pipe_col_kernel<LOGN, true, 0> : pipe_col_kernel<LOGN, false, 0>));
@@ -722,6 +1052,10 @@ cudaError_t launch_plane2(int64_t O, const float2 *in, float2 *out, const Twiddl
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     }
+    if (col2_enabled() && (reinterpret_cast<uintptr_t>(out) & 15) == 0)
+        return launch_maybe_dependent(pipe_col2_kernel<false, 3>, grid, 512, col_smem<12>(), stream,
+                                      flags & FLAG_PDL, maps[0], maps[1], omap, out, 256, 10, ntiles, tw.stage[12],
+                                      tw.lo, tw.hi, tw.h, flags, staged, status);
     return launch_maybe_dependent(pipe_col_kernel<12, false, 3>, grid, 1024, col_smem<12>(), stream, flags & FLAG_PDL,
                                   maps[0], maps[1], omap, out, 256, 10, ntiles, tw.stage[12], tw.lo, tw.hi, tw.h,
                                   flags, staged, status);
@@ -756,6 +1090,8 @@ cudaError_t set_pipe_attrs()
 
 bool pipe_supported() { return encode_fn() != nullptr; }
 
+bool pipe_col2_active() { return col2_enabled(); }
+
 bool encode_c64_map(CUtensorMap *map, const void *base, int rank, const uint64_t *dims, const uint64_t *strides,
                     const uint32_t *box)
 {
@@ -789,8 +1125,13 @@ cudaError_t prepare_pipe_kernels()
         __atomic_store_n(&g_num_sms[dev], nsm, __ATOMIC_RELAXED);
     if ((e = set_pipe_attrs<10>()) || (e = set_pipe_attrs<11>()) || (e = set_pipe_attrs<12>()))
         return e;
-    if ((e = cudaFuncSetAttribute(pipe_col_kernel<12, false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)col_smem<12>())))
+    const int cs = (int)col_smem<12>();
+    if ((e = cudaFuncSetAttribute(pipe_col_kernel<12, false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) ||
+        (e = cudaFuncSetAttribute(pipe_col2_kernel<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) ||
+        (e = cudaFuncSetAttribute(pipe_col2_kernel<false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) ||
+        (e = cudaFuncSetAttribute(pipe_col2_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) ||
+        (e = cudaFuncSetAttribute(pipe_col2_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) ||
+        (e = cudaFuncSetAttribute(pipe_col2_kernel<false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs)))
         return e;
     return cudaSuccess;
 }

@@ -105,7 +105,7 @@ def test_plan_log(env, tmp_path):
     lines = [ln for ln in res.stderr.splitlines() if ln.startswith("moafft: ")]
     cands = [ln for ln in lines if ln.startswith("moafft: autotune candidate ")]
     # 1-D 2^17: splits 2^5..2^12, with pipelined and generic kernels and three tiles
-    assert sum("col_pass_kernel<" in ln or "pipe_col_kernel<" in ln for ln in cands) >= 8, lines
+    assert sum("col_pass_kernel<" in ln or "pipe_col" in ln for ln in cands) >= 8, lines
     # 2-D 64 x 32: the tile sizes of its two generic passes
     assert any("row_pass_kernel<5,0>/" in ln and "col_pass_kernel<6,0>/" in ln for ln in cands), lines
     plan_lines = [ln for ln in lines if ln.startswith("moafft: plan ")]

@@ -223,7 +223,9 @@ def test_blocked_workspace_lifted(env, L, lr, batch, sign, monkeypatch):
     x = inputs.uniform((batch, n), 6100 + L + lr)
     plan = moafft.Plan([n], batch, sign)
     names = [plan.pass_info(i)["kernel"] for i in range(plan.info()["passes"])]
-    assert names == ["pipe_col_kernel<%d,1,1>" % lr, "pipe_col_kernel<%d,0,2>" % (L - lr)], names
+    def pipe_col(logn, tw4, blk):   # two columns per thread at N = 4096
+        return "pipe_col2_kernel<%d,%d>" % (tw4, blk) if logn == 12 else "pipe_col_kernel<%d,%d,%d>" % (logn, tw4, blk)
+    assert names == [pipe_col(lr, 1, 1), pipe_col(L - lr, 0, 2)], names
     y = plan.exec(torch.from_numpy(x).cuda()).cpu().numpy()
     assert plan.status() == 0
     plan.destroy()
@@ -299,6 +301,35 @@ def test_pdl_chain_across_plans(env, monkeypatch):
     assert np.isfinite(ref).all()
     assert np.array_equal(got, ref)
     assert np.array_equal(again, ref)
+
+
+@pytest.mark.parametrize("shape,batch", [((1 << 24,), 1), ((4096, 4096), 1), ((256, 256, 256), 1), ((4096, 8), 2)])
+def test_output_only_eight_byte_aligned(env, shape, batch):
+    """A 16-byte aligned input with an output one complex64 past a 16-byte
+    boundary.  1-D 2^24 and 3-D 256^3: the last pass reads the aligned
+    workspace and writes the output through the four-column N = 4096 kernel
+    (8-byte plain stores), whose arithmetic is that of the two-column one:
+    the results equal those of the aligned output bit for bit.  2-D: the
+    column pass reads the misaligned output in place, so the generic kernel
+    runs.  Every case matches the oracle."""
+    torch, moafft, _ = env
+    from paper_0811_2535_gb300 import inputs
+    n = int(np.prod(shape)) * batch
+    x = inputs.uniform((batch,) + shape, 6700 + n % 991)
+    xin = torch.from_numpy(x.reshape(-1)).cuda()
+    assert xin.data_ptr() % 16 == 0
+    bout = torch.empty(n + 1, dtype=torch.complex64, device="cuda")
+    yout = bout[1:]
+    assert yout.data_ptr() % 16 == 8
+    plan = moafft.Plan(list(shape), batch, -1)
+    plan.exec(xin, out=yout)
+    aligned = plan.exec(xin).cpu().numpy()
+    assert plan.status() == 0
+    plan.destroy()
+    y = yout.cpu().numpy()
+    if len(shape) != 2:
+        assert np.array_equal(y, aligned)
+    assert per_transform_rel(y, oracle_ref(env, x, list(shape), batch, -1), batch).max() <= TOL
 
 
 @pytest.mark.parametrize("shape,batch", [((1 << 24,), 1), ((1 << 22,), 2), ((1 << 20,), 3), ((1 << 13,), 5),
@@ -380,7 +411,7 @@ def test_3d_two_pass(env, batch, sign, monkeypatch):
     plan = moafft.Plan(list(shape), batch, sign)
     names = [plan.pass_info(i)["kernel"] for i in range(plan.info()["passes"])]
     plan.destroy()
-    assert names == ["plane3d_p1_kernel", "pipe_col_kernel<12,0,3>"], names
+    assert names == ["plane3d_p1_kernel", "pipe_col2_kernel<0,3>"], names
     y, _ = run(env, list(shape), batch, sign, x)
     yi, _ = run(env, list(shape), batch, sign, x, inplace=True)
     monkeypatch.setenv("MOA_3D_TWO_PASS", "0")

@@ -9,6 +9,12 @@ import pytest
 TMA, NO_TMA = 1, 0
 
 
+def pipe_col(logn, tw4, blk):
+    """Name of the pipelined column kernel of a pass: at N = 4096 the
+    two-columns-per-thread form, below it the four-column form."""
+    return f"pipe_col2_kernel<{tw4},{blk}>" if logn == 12 else f"pipe_col_kernel<{logn},{tw4},{blk}>"
+
+
 @pytest.fixture(scope="module")
 def mf():
     from paper_0811_2535_gb300 import build, moafft
@@ -35,20 +41,20 @@ def test_1d_lifting(mf, L, batch):
         assert e["passes"] == 2 and e["workspace_bytes"] == 8 * batch << L
         pipe_r, pipe_c = tma == TMA and 10 <= lr <= 12, tma == TMA and 10 <= lc <= 12
         if pipe_r and pipe_c:
-            assert e["kernels"] == [f"pipe_col_kernel<{lr},1,1>", f"pipe_col_kernel<{lc},0,2>"]
+            assert e["kernels"] == [pipe_col(lr, 1, 1), pipe_col(lc, 0, 2)]
         else:
             assert e["kernels"] == [f"col_pass_kernel<{lr},1>",
                                     f"pipe_rowT_kernel<{lc}>" if pipe_c else f"row_pass_kernel<{lc},1>"]
 
 
 def test_bench_workload_plans(mf):
-    assert mf.estimate([1 << 24], tma=TMA)["kernels"] == ["pipe_col_kernel<12,1,1>", "pipe_col_kernel<12,0,2>"]
+    assert mf.estimate([1 << 24], tma=TMA)["kernels"] == ["pipe_col2_kernel<1,1>", "pipe_col2_kernel<0,2>"]
     assert mf.estimate([4096, 4096], tma=TMA) == {
         "passes": 2, "split_r": 0, "split_c": 0, "workspace_bytes": 0,
-        "kernels": ["row_pass_kernel<12,0>", "pipe_col_kernel<12,0,0>"]}
+        "kernels": ["row_pass_kernel<12,0>", "pipe_col2_kernel<0,0>"]}
     assert mf.estimate([256, 256, 256], tma=TMA) == {
         "passes": 2, "split_r": 0, "split_c": 0, "workspace_bytes": 8 << 24,
-        "kernels": ["plane3d_p1_kernel", "pipe_col_kernel<12,0,3>"]}
+        "kernels": ["plane3d_p1_kernel", "pipe_col2_kernel<0,3>"]}
 
 
 @pytest.mark.parametrize("shape,batch", [((2, 2), 1), ((8, 16), 5), ((64, 32), 2), ((4096, 2), 1), ((2, 4096), 3),
@@ -65,7 +71,7 @@ def test_multi_d_one_pass_per_axis(mf, shape, batch):
 
 def test_environment_overrides(mf, monkeypatch):
     monkeypatch.setenv("MOA_PIPE", "1")   # pipelined kernels, natural intermediate
-    assert mf.estimate([1 << 24], tma=TMA)["kernels"] == ["pipe_col_kernel<12,1,0>", "pipe_rowT_kernel<12>"]
+    assert mf.estimate([1 << 24], tma=TMA)["kernels"] == ["pipe_col2_kernel<1,0>", "pipe_rowT_kernel<12>"]
     monkeypatch.setenv("MOA_PIPE", "0")   # generic kernels only, and one pass per axis in 3-D
     assert mf.estimate([1 << 24], tma=TMA)["kernels"] == ["col_pass_kernel<12,1>", "row_pass_kernel<12,1>"]
     assert mf.estimate([256, 256, 256], tma=TMA)["passes"] == 3
@@ -77,7 +83,7 @@ def test_environment_overrides(mf, monkeypatch):
     monkeypatch.setenv("MOA_SPLIT_LOG2R", "10")
     e = mf.estimate([1 << 22], tma=TMA)
     assert (e["split_r"], e["split_c"]) == (1024, 4096)
-    assert e["kernels"] == ["pipe_col_kernel<10,1,1>", "pipe_col_kernel<12,0,2>"]
+    assert e["kernels"] == ["pipe_col_kernel<10,1,1>", "pipe_col2_kernel<0,2>"]
     e = mf.estimate([1 << 24], tma=TMA)   # c would be 2^14: out of range, default split kept
     assert (e["split_r"], e["split_c"]) == (4096, 4096)
     monkeypatch.delenv("MOA_SPLIT_LOG2R")
@@ -156,3 +162,20 @@ def test_multi_d_long_axes(mf, shape, batch, kernels):
         n *= s_
     assert e["kernels"] == kernels
     assert (e["passes"], e["workspace_bytes"]) == (len(kernels), 8 * n)
+
+
+def test_four_column_kernel_on_request():
+    """MOA_COL2=0 (read once per process, so checked in a child process):
+    the N = 4096 column passes name the four-column kernel."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_0811_2535_gb300 import moafft\n"
+            "print(moafft.estimate([1 << 24], tma=1)['kernels'], moafft.estimate([256] * 3, tma=1)['kernels'])\n") % root
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300,
+                         env=dict(os.environ, MOA_COL2="0"))
+    assert res.returncode == 0, res.stderr
+    assert res.stdout.strip() == ("['pipe_col_kernel<12,1,1>', 'pipe_col_kernel<12,0,2>'] "
+                                  "['plane3d_p1_kernel', 'pipe_col_kernel<12,0,3>']")
