@@ -141,14 +141,17 @@ struct PipeSmem {
     {
         return (size_t)(E_entries<LOGN>() + H_entries<LOGN>() + 64) * 8 + 64;
     }
+    // column kernel: per-tile twiddle tables behind H (three tables of
+    // [16][4] entries: the four-step factors of the tile's columns)
+    static constexpr int kTwEntries = 192;
     // column kernel: rows of the next tile that land early (while the tile
     // computes) in a buffer of their own; the rest lands in the exchange
     // buffer after its last use.  As many whole 256-row boxes as fit next to
-    // the exchange buffer, at most all but one.
+    // the exchange buffer and the tables, at most all but one.
     template <int LOGN> __host__ __device__ static constexpr int early_rows()
     {
-        return ((((232448 - E_entries<LOGN>() * 8 - 1280) / 32) / 256) * 256) < (1 << LOGN) - 256
-                   ? (((232448 - E_entries<LOGN>() * 8 - 1280) / 32) / 256) * 256
+        return ((((232448 - E_entries<LOGN>() * 8 - kTwEntries * 8 - 64) / 32) / 256) * 256) < (1 << LOGN) - 256
+                   ? (((232448 - E_entries<LOGN>() * 8 - kTwEntries * 8 - 64) / 32) / 256) * 256
                    : (1 << LOGN) - 256;
     }
 };
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
     float2 *H = E + PipeSmem::E_entries<LOGN>();
     constexpr int HR = PipeSmem::early_rows<LOGN>();   // rows landing in H; rows HR..N-1 land in E
     float2 *tk = H + 4 * HR;                           // [16][4] four-step twiddle factors
-    uint64_t *bar = reinterpret_cast<uint64_t *>(tk + 64);   // [0]: H, [1]: the rest in E
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tk + PipeSmem::kTwEntries);   // [0]: H, [1]: the rest in E
     int *abort_flag = reinterpret_cast<int *>(bar + 2);
 
     const int tid = threadIdx.x;
@@ -539,8 +542,11 @@ __global__ void __launch_bounds__(512, 1)
     float2 *E = reinterpret_cast<float2 *>(smem_raw);
     float2 *H = E + PipeSmem::E_entries<12>();
     constexpr int HR = PipeSmem::early_rows<12>();   // rows landing in H; rows HR..N-1 land in E
-    float2 *tk = H + 4 * HR;                         // [16][4] four-step twiddle factors
-    uint64_t *bar = reinterpret_cast<uint64_t *>(tk + 64);
+    // four-step twiddle tables of the tile, [16][4] each (entry i*4 + f for
+    // column c0 + f): tl[i] = w^(col*i), th[i] = w^(col*16i), tk[i] = w^(col*256i),
+    // so that w^(col*(tau + 256k)) = tl[tau % 16] * th[tau / 16] * tk[k]
+    float2 *twt = H + 4 * HR;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(twt + PipeSmem::kTwEntries);
     int *abort_flag = reinterpret_cast<int *>(bar + 2);
     float4 *E4 = reinterpret_cast<float4 *>(E);
     const float4 *H4 = reinterpret_cast<const float4 *>(H);
@@ -570,6 +576,18 @@ __global__ void __launch_bounds__(512, 1)
         const int next = tile + (int)gridDim.x;
         if (next >= ntiles)
             pdl_launch_dependents();   // the block's last tile: let the next kernel launch
+        // the tile's twiddle table entries (threads below 192, one each, from
+        // the two-level table), loaded before the tile wait so that their
+        // latency is spent behind it
+        float2 el, eh;
+        if constexpr (TW4) {
+            if (tid < PipeSmem::kTwEntries) {
+                const int j = tid >> 6, i = (tid >> 2) & 15;
+                const int64_t e = (int64_t)(c0 + (tid & 3)) * (i << (4 * j));
+                el = __ldg(&tw_lo[e & ((int64_t(1) << tw_h) - 1)]);
+                eh = __ldg(&tw_hi[e >> tw_h]);
+            }
+        }
         if (tid == 0) {
             bounded_wait(&bar[0], parity, status, abort_flag, flags);
             bounded_wait(&bar[1], parity, status, abort_flag, flags);
@@ -607,9 +625,8 @@ __global__ void __launch_bounds__(512, 1)
             }
         }
         if constexpr (TW4) {
-            // tk[k][f] = w^(column f * T*k), 64 entries, one per thread of the first 64
-            if (tid < 64)
-                tk[tid] = two_level_tw(tw_lo, tw_hi, tw_h, (int64_t)(c0 + (tid & 3)) * (T * (tid >> 2)));
+            if (tid < PipeSmem::kTwEntries)
+                twt[tid] = cmul(el, eh);
         }
 
         stage_compute2<0, BLK != 3>(v, u, tau, tw);
@@ -629,13 +646,14 @@ __global__ void __launch_bounds__(512, 1)
         stage_compute2<2>(v, u, tau, tw);
 
         if constexpr (TW4) {
-            // w^(col * (tau + T*k)) = A * tk[k][col]
-            const float2 A0 = two_level_tw(tw_lo, tw_hi, tw_h, (int64_t)col * tau);
-            const float2 A1 = two_level_tw(tw_lo, tw_hi, tw_h, (int64_t)(col + 1) * tau);
-            const float4 *tk4 = reinterpret_cast<const float4 *>(tk);
+            // w^(col * (tau + T*k)) = A * tk[k][col], A = tl[tau % 16][col] * th[tau / 16][col]
+            const float4 *t4 = reinterpret_cast<const float4 *>(twt);
+            const float4 l = t4[(tau & 15) * 2 + g], h = t4[32 + (tau >> 4) * 2 + g];
+            const float2 A0 = cmul(make_float2(l.x, l.y), make_float2(h.x, h.y));
+            const float2 A1 = cmul(make_float2(l.z, l.w), make_float2(h.z, h.w));
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
-                const float4 t = tk4[k * 2 + g];
+                const float4 t = t4[64 + k * 2 + g];
                 v[k] = cmul(v[k], cmul(A0, make_float2(t.x, t.y)));
                 u[k] = cmul(u[k], cmul(A1, make_float2(t.z, t.w)));
             }
@@ -866,7 +884,7 @@ EncodeTiledFn encode_fn()
 // mbarriers and a flag
 template <int LOGN> size_t col_smem()
 {
-    return (size_t)(PipeSmem::E_entries<LOGN>() + 4 * PipeSmem::early_rows<LOGN>() + 64) * 8 + 64;
+    return (size_t)(PipeSmem::E_entries<LOGN>() + 4 * PipeSmem::early_rows<LOGN>() + PipeSmem::kTwEntries) * 8 + 64;
 }
 template <int LOGN> size_t rowT_smem() { return PipeSmem::bytes<LOGN>(); }
 
