@@ -113,6 +113,21 @@ __device__ __forceinline__ void large_col_tile(const float2 *x, float2 *b, int c
         dst[(int64_t)k * T * c] = cmul(v[k], two_level_b(lo, hi, h, (int64_t)col * (tau + T * k)));
 }
 
+// The workspace lines a row tile has read are not needed again (each is read
+// by exactly one row tile): drop them from L2 without a write-back, so that
+// the column-pass results never travel to DRAM.  Only whole 128-byte lines
+// inside the region [p, p + n) are dropped (a transform's offset in the batch
+// is only 16-byte aligned).  The caller has consumed every load of the
+// region in every thread before the call (a block barrier after their use).
+__device__ __forceinline__ void discard_read_lines(const float2 *p, int64_t n)
+{
+    uint64_t a;
+    asm("cvta.to.global.u64 %0, %1;" : "=l"(a) : "l"(p));
+    const uint64_t first = (a + 127) & ~uint64_t(127), last = (a + (uint64_t)n * sizeof(float2)) & ~uint64_t(127);
+    for (uint64_t l = first + (uint64_t)threadIdx.x * 128; l < last; l += (uint64_t)blockDim.x * 128)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(l) : "memory");
+}
+
 // One row tile of a large transform: c = 2^LOGC points per row, 4096/c
 // rows starting at row 4096/c * tile, transposed store into X (r rows).  The
 // rows are read with c/16 consecutive threads per row (whole runs of one row
@@ -141,6 +156,8 @@ __device__ __forceinline__ void large_row_tile(const float2 *b, float2 *X, int r
         for (int q = 0; q < Sc::P; ++q)
             v[q] = src[q];
         stage_compute<LOGC, 0>(v, 0, tb.stage[LOGC]);
+        __syncthreads();   // every load of the tile has been used
+        discard_read_lines(b + (int64_t)tile * F * N, (int64_t)F * N);
     } else {
         const int tau_a = tid & (T - 1), fa = tid >> LOGT;
         const float2 *src = b + (int64_t)(tile * F + fa) * N + tau_a;
@@ -149,7 +166,8 @@ __device__ __forceinline__ void large_row_tile(const float2 *b, float2 *X, int r
             v[(q % NB0) * R0 + q / NB0] = src[q * T];
         stage_compute<LOGC, 0>(v, tau_a, tb.stage[LOGC]);
         stage_write<LOGC, 0, LR>(v, sm, tau_a, fa);
-        __syncthreads();
+        __syncthreads();   // also: every load of the tile has been used
+        discard_read_lines(b + (int64_t)tile * F * N, (int64_t)F * N);
         stage_read<LOGC, 1, LR>(v, sm, tau_b, fb);
         __syncthreads();
         stage_compute<LOGC, 1>(v, tau_b, tb.stage[LOGC]);
