@@ -588,35 +588,83 @@ __global__ void __launch_bounds__(512, 1)
                 eh = __ldg(&tw_hi[e >> tw_h]);
             }
         }
-        if (tid == 0) {
-            bounded_wait(&bar[0], parity, status, abort_flag, flags);
-            bounded_wait(&bar[1], parity, status, abort_flag, flags);
-            if (*abort_flag)
-                drain_in_flight(bar, parity);
-        }
-        __syncthreads();
-        if (*abort_flag) {
-            if (staged && tid == 0)
-                bulk_wait_all();   // no staged store may still read E
-            return;
-        }
-        parity ^= 1u;
-
         // element tau + T*q of both columns (rows below HR in H, the others in E)
         float2 v[16], u[16];
+        if constexpr (BLK == 1) {
+            // Lifted pass 1 drains its staged outputs as three 32 KiB stores,
+            // which may still be reading E when the next tile has landed.  The
+            // early rows are read as soon as they are in; the late rows (in E)
+            // after their own wait, while the next tile's early rows are already
+            // on their way into H; the wait for the staged stores comes just
+            // before the first exchange writes E.  (Measured: pass 1 61.3 ->
+            // 58.8 us; for the row-output passes, whose twelve 8 KiB stores have
+            // left E by then, the extra barrier costs 0.7-2.6 us.)
+            if (tid == 0) {
+                bounded_wait(&bar[0], parity, status, abort_flag, flags);
+                if (*abort_flag)
+                    drain_in_flight(bar, parity);
+            }
+            __syncthreads();
+            if (*abort_flag) {
+                if (staged && tid == 0)
+                    bulk_wait_all();   // no staged store may still read E
+                return;
+            }
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const float4 a = q * T < HR ? H4[(tau + T * q) * 2 + g] : E4[(tau + T * q - HR) * 2 + g];
-            v[q] = make_float2(a.x, a.y);
-            u[q] = make_float2(a.z, a.w);
+            for (int q = 0; q * T < HR; ++q) {
+                const float4 a = H4[(tau + T * q) * 2 + g];
+                v[q] = make_float2(a.x, a.y);
+                u[q] = make_float2(a.z, a.w);
+            }
+            if (tid == 0) {
+                bounded_wait(&bar[1], parity, status, abort_flag, flags);
+                if (*abort_flag)
+                    drain_in_flight(bar, parity);
+            }
+            __syncthreads();   // H has been read; the late rows have landed
+            if (*abort_flag) {
+                if (staged && tid == 0)
+                    bulk_wait_all();
+                return;
+            }
+            if (tid == 0 && next < ntiles) {
+                fence_proxy_async();
+                issue_tile_part<12, BLK>(&tmapH, &tmapE, logTpo, next, 0, H, &bar[0]);
+            }
+#pragma unroll
+            for (int q = HR / T; q < 16; ++q) {
+                const float4 a = E4[(tau + T * q - HR) * 2 + g];
+                v[q] = make_float2(a.x, a.y);
+                u[q] = make_float2(a.z, a.w);
+            }
+        } else {
+            if (tid == 0) {
+                bounded_wait(&bar[0], parity, status, abort_flag, flags);
+                bounded_wait(&bar[1], parity, status, abort_flag, flags);
+                if (*abort_flag)
+                    drain_in_flight(bar, parity);
+            }
+            __syncthreads();
+            if (*abort_flag) {
+                if (staged && tid == 0)
+                    bulk_wait_all();   // no staged store may still read E
+                return;
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float4 a = q * T < HR ? H4[(tau + T * q) * 2 + g] : E4[(tau + T * q - HR) * 2 + g];
+                v[q] = make_float2(a.x, a.y);
+                u[q] = make_float2(a.z, a.w);
+            }
+            if (staged && tid == 0)
+                bulk_wait_read();   // the previous tile's staged outputs have left E
+            __syncthreads();   // H and E have been read
+            if (tid == 0 && next < ntiles) {
+                fence_proxy_async();
+                issue_tile_part<12, BLK>(&tmapH, &tmapE, logTpo, next, 0, H, &bar[0]);
+            }
         }
-        if (staged && tid == 0)
-            bulk_wait_read();   // the previous tile's staged outputs have left E
-        __syncthreads();   // H and E have been read
-        if (tid == 0 && next < ntiles) {
-            fence_proxy_async();
-            issue_tile_part<12, BLK>(&tmapH, &tmapE, logTpo, next, 0, H, &bar[0]);
-        }
+        parity ^= 1u;
         if (flags & FLAG_CONJ_IN) {
 #pragma unroll
             for (int r = 0; r < 16; ++r) {
@@ -630,6 +678,14 @@ __global__ void __launch_bounds__(512, 1)
         }
 
         stage_compute2<0, BLK != 3>(v, u, tau, tw);
+        if constexpr (BLK == 1) {
+            // the previous tile's staged outputs must have left E, and every
+            // thread have read its late rows from E, before the first
+            // exchange writes it
+            if (staged && tid == 0)
+                bulk_wait_read();
+            __syncthreads();
+        }
         stage_write2<0>(v, u, E4, tau, g);
         __syncthreads();
         stage_read2<1>(v, u, E4, tau, g);
@@ -1022,7 +1078,8 @@ cudaError_t launch_col(const PassDesc &d, int64_t O, int64_t C, int blk, const f
                               : (d.tw4 && blk == 1 ? pipe_col2_kernel<true, 1>
                                                    : (d.tw4 ? pipe_col2_kernel<true, 0> : pipe_col2_kernel<false, 0>));
         return launch_maybe_dependent(kern2, grid, 512, smem, stream, flags & FLAG_PDL, maps[0], maps[1], omap, out,
-                                      Ci, logTpo, ntiles, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags, staged, status);
+                                      Ci, logTpo, ntiles, tw.stage[LOGN], tw.lo, tw.hi, tw.h, flags,
+                                      staged, status);
     }
     auto kern = blk == 2 ? pipe_col_kernel<LOGN, false, 2>
                          : (d.tw4 && blk == 1 ? pipe_col_kernel<LOGN, true, 1>
