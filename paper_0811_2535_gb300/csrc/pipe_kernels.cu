@@ -107,6 +107,12 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void 
                  : "memory");
 }
 
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void *src, int x, int y, int z)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
+                 "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+                 : "memory");
+}
 __device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, const void *src, int x, int y, int z, int w)
 {
     asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(map),
@@ -538,6 +544,8 @@ __global__ void __launch_bounds__(512, 1)
                      const float2 *__restrict__ tw_hi, int tw_h, int flags, int staged, int *status)
 {
     constexpr int N = 4096, T = 256;
+    // landing order: the split order for lifted pass 1 (see the tile start)
+    constexpr bool kSplitLanding = BLK == 1;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     float2 *E = reinterpret_cast<float2 *>(smem_raw);
     float2 *H = E + PipeSmem::E_entries<12>();
@@ -590,7 +598,7 @@ __global__ void __launch_bounds__(512, 1)
         }
         // element tau + T*q of both columns (rows below HR in H, the others in E)
         float2 v[16], u[16];
-        if constexpr (BLK == 1) {
+        if constexpr (kSplitLanding) {
             // Lifted pass 1 drains its staged outputs as three 32 KiB stores,
             // which may still be reading E when the next tile has landed.  The
             // early rows are read as soon as they are in; the late rows (in E)
@@ -678,7 +686,7 @@ __global__ void __launch_bounds__(512, 1)
         }
 
         stage_compute2<0, BLK != 3>(v, u, tau, tw);
-        if constexpr (BLK == 1) {
+        if constexpr (kSplitLanding) {
             // the previous tile's staged outputs must have left E, and every
             // thread have read its late rows from E, before the first
             // exchange writes it
@@ -789,12 +797,14 @@ __global__ void __launch_bounds__(512, 1)
                     for (int j = 0; j < 3; ++j)
                         tma_store_2d(&omap, stg + j * 256 * 16, 0, b0 + 256 * j);
                 } else {
+                    // three boxes of four slices (32 KiB) each
+                    static_assert(KS == 12, "twelve staged slices");
 #pragma unroll 1
-                    for (int k = 0; k < KS; ++k) {
+                    for (int j = 0; j < 3; ++j) {
                         if constexpr (BLK == 3)
-                            tma_store_4d(&omap, stg + k * 4 * T, 2 * (c0 & 255), c0 >> 8, 0, o * 256 + 16 * k);
+                            tma_store_4d(&omap, stg + j * 16 * T, 2 * (c0 & 255), c0 >> 8, 0, o * 256 + 64 * j);
                         else
-                            tma_store_2d(&omap, stg + k * 4 * T, 2 * c0, o * N + T * k);
+                            tma_store_3d(&omap, stg + j * 16 * T, 2 * c0, 0, o * (N / 256) + 4 * j);
                     }
                 }
                 bulk_commit();
@@ -1000,6 +1010,24 @@ bool encode_out_rows(CUtensorMap *map, float2 *out, int64_t O, int64_t C, int lo
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Output tensor map of the two-column kernel's staged row stores over the
+// [O][N][C] view: {2C floats, 256 rows, O*N/256 row blocks}, boxes of 4
+// columns x 256 rows x 4 row blocks (four slices, 32 KiB).  False when the
+// output cannot be a TMA target (not 16-byte aligned).
+bool encode_out_rows4(CUtensorMap *map, float2 *out, int64_t O, int64_t C, int logN)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc || (reinterpret_cast<uintptr_t>(out) & 15) != 0)
+        return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)(2 * C), 256, (cuuint64_t)((O << logN) >> 8)};
+    const cuuint64_t strides[2] = {(cuuint64_t)(2 * C * sizeof(float)), (cuuint64_t)(256 * 2 * C * sizeof(float))};
+    const cuuint32_t box[3] = {8, 256, 4};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, out, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Output tensor map of the two-column kernel's staged blocked stores: the
 // blocked workspace as {32 floats (one 4 x 4 block), blocks}, boxes of 256
 // blocks, 128-byte swizzle.  False when it cannot be encoded.
@@ -1072,8 +1100,9 @@ cudaError_t launch_col(const PassDesc &d, int64_t O, int64_t C, int blk, const f
     if (LOGN == 12 && staged_enabled())
         staged = blk == 1 ? (reinterpret_cast<uintptr_t>(out) & 15) == 0 : encode_out_rows(&omap, out, O, C, LOGN);
     if (LOGN == 12 && col2_enabled() && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
-        if (blk == 1 && staged)
-            staged = encode_out_blocked(&omap, out, (O << LOGN) * C / 16);
+        if (staged)
+            staged = blk == 1 ? encode_out_blocked(&omap, out, (O << LOGN) * C / 16)
+                              : encode_out_rows4(&omap, out, O, C, LOGN);
         auto kern2 = blk == 2 ? pipe_col2_kernel<false, 2>
                               : (d.tw4 && blk == 1 ? pipe_col2_kernel<true, 1>
                                                    : (d.tw4 ? pipe_col2_kernel<true, 0> : pipe_col2_kernel<false, 0>));
@@ -1121,7 +1150,8 @@ cudaError_t launch_plane2(int64_t O, const float2 *in, float2 *out, const Twiddl
         const cuuint64_t odims[4] = {512, 16, 16, (cuuint64_t)(O * 256)};
         const cuuint64_t ostrides[3] = {256 * sizeof(float2), 16 * 256 * sizeof(float2),
                                         65536 * sizeof(float2)};
-        const cuuint32_t obox[4] = {8, 1, 16, 16};
+        const bool two = col2_enabled();   // (the two-column kernel stores four slices per box)
+        const cuuint32_t obox[4] = {8, 1, 16, two ? 64u : 16u};
         const cuuint32_t oestr[4] = {1, 1, 1, 1};
         staged = enc(&omap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, out, odims, ostrides, obox, oestr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
