@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(const float2 *in, float2
 // w_256^(j1a*k1b); the result for k1b goes to row j1a + 16*k1b of the
 // workspace.  The second pass (the DFT over j1a and the axis-0 transform)
 // runs in pipe_col_kernel<12, false, 3>.
-__global__ void __launch_bounds__(256) plane3d_p1_kernel(const float2 *in, float2 *ws, int ntiles,
+__global__ void __launch_bounds__(256, 5) plane3d_p1_kernel(const float2 *in, float2 *ws, int ntiles,
                                                          const float2 *__restrict__ tw8,
                                                          const float2 *__restrict__ w256, int flags)
 {
