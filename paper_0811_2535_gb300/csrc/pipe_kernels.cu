@@ -770,14 +770,18 @@ __global__ void __launch_bounds__(512, 1)
                 // 128-byte swizzle of the output tensor map (16-byte chunk j of
                 // block b at chunk j ^ (b % 8)), so that the blocks of a warp's
                 // four tau groups fall on different banks; b % 8 = (tau/4) % 8
+                // The 8-byte stores are served per half-warp (two blocks): lanes
+                // of odd blocks store their second column first, so that the
+                // two blocks of a half-warp fill disjoint chunks in each store.
                 char *sb = reinterpret_cast<char *>(stg) + (tau >> 2) * 128 + (tau & 1) * 8;
                 const int sw = (tau >> 2) & 7, ch = 4 * g + ((tau >> 1) & 1);   // chunk of the first column
-                float2 *p0 = reinterpret_cast<float2 *>(sb + ((ch ^ sw) << 4));
-                float2 *p1 = reinterpret_cast<float2 *>(sb + (((ch + 2) ^ sw) << 4));
+                const bool odd = ((tau >> 2) & 1) != 0;
+                float2 *p0 = reinterpret_cast<float2 *>(sb + (((odd ? ch + 2 : ch)) ^ sw) * 16);
+                float2 *p1 = reinterpret_cast<float2 *>(sb + (((odd ? ch : ch + 2)) ^ sw) * 16);
 #pragma unroll
                 for (int k = 0; k < KS; ++k) {
-                    p0[k * 4 * T] = v[k];
-                    p1[k * 4 * T] = u[k];
+                    p0[k * 4 * T] = odd ? u[k] : v[k];
+                    p1[k * 4 * T] = odd ? v[k] : u[k];
                 }
             } else {
                 float4 *sp = reinterpret_cast<float4 *>(stg) + tau * 2 + g;
