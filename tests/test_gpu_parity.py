@@ -398,6 +398,20 @@ def test_cuda_graph_of_dependent_launches(env, shape, batch):
     inv.destroy()
 
 
+@pytest.mark.parametrize("shape,batch", [((1 << 24,), 2), ((1 << 23,), 2), ((4096, 4096), 2)])
+def test_two_column_kernels_batched(env, shape, batch):
+    """The N = 4096 column passes (two columns per thread) over several
+    transforms in one launch: the tile's transform index o enters the landing
+    coordinates, the staged-store boxes (blocked output of the lifted pass 1,
+    row blocks of the others) and the plain stores.  2^24 and 2^23 use them
+    for both or the second lifted pass, 4096^2 for its column axis."""
+    from paper_0811_2535_gb300 import inputs
+    x = inputs.uniform((batch,) + shape, 6900 + len(shape) + batch)
+    y, _ = run(env, list(shape), batch, -1, x)
+    ref = oracle_ref(env, x, list(shape), batch, -1)
+    assert per_transform_rel(y, ref, batch).max() <= TOL
+
+
 @pytest.mark.parametrize("batch", [1, 2])
 @pytest.mark.parametrize("sign", [-1, 1])
 def test_3d_two_pass(env, batch, sign, monkeypatch):
