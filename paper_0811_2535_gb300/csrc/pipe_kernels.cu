@@ -462,10 +462,14 @@ __global__ void __launch_bounds__(1 << (LOGN - 2), 1)
 // holds columns 2g and 2g+1 in v and u.  The shared-memory layouts stay those
 // of the four-column kernel (element e of column f at byte 32*pad16(e) + 8f),
 // in which the two columns of a thread are 16 contiguous bytes: every
-// landing, exchange and staging access moves a float4, half the shared-memory
-// instructions; the stage twiddle rows are loaded and their products formed
-// once for both columns.  The arithmetic of each column is that of the
-// four-column kernel, operation for operation.
+// landing and exchange access, and the staging of row outputs, moves a float4
+// (half the shared-memory instructions; the blocked staging of lifted pass 1
+// is two 8-byte stores, the two columns being 32 bytes apart in a 4 x 4
+// block); the stage twiddle rows are loaded and their products formed once
+// for both columns.  The arithmetic of each column is that of the
+// four-column kernel, operation for operation.  Lifted pass 1 (BLK = 1) also
+// differs in its four-step twiddle tables and its landing order (see the
+// kernel).
 
 // Stage s of the three radix-16 stages on the two transforms of a thread;
 // TWID = false leaves out the stage twiddles (as stage_compute does).
