@@ -492,6 +492,60 @@ def small_report(torch, moafft, inputs, dev, iters):
     return out
 
 
+def schedules_report(torch, moafft, dev, iters, peak):
+    """Radix schedules of the in-register stages (Sec. 4.8: any factorisation
+    is valid) on batched rows of 2^25 points (256 MiB in, 256 MiB out):
+    0 = radix 16 with the small radix first, 1 = small radix last, 2 =
+    radix-8 stages, 3 = warp-shuffle kernel (cross-lane butterflies by
+    shfl.xor, no shared-memory exchange); then what the autotuner keeps."""
+    saved = {k: os.environ.get(k) for k in ("MOA_SCHED", "MOA_AUTOTUNE")}
+    out = {}
+    try:
+        for L in (9, 11):
+            n, batch = 1 << L, (1 << 25) >> L
+            x = torch.randn(n * batch, dtype=torch.complex64, device=dev)
+            y = torch.empty_like(x)
+            stream = torch.cuda.current_stream(dev)
+            res = {}
+            os.environ["MOA_AUTOTUNE"] = "0"
+            for v in (0, 1, 2, 3):
+                os.environ["MOA_SCHED"] = str(v)
+                plan = moafft.Plan([n], batch, -1)
+                kern = plan.pass_info(0)["kernel"]
+                if any(r["kernel"] == kern for r in res.values()):
+                    plan.destroy()
+                    continue   # the schedule does not exist for this length
+                for _ in range(3):
+                    plan.exec(x, y, stream=stream)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(iters):
+                    plan.exec(x, y, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                us = e0.elapsed_time(e1) / iters * 1e3
+                res[str(v)] = {"kernel": kern, "us": us, "frac": 16.0 * n * batch / (us * 1e3) / peak}
+                plan.destroy()
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+            plan = moafft.Plan([n], batch, -1)
+            res["autotuned"] = plan.choice()
+            plan.destroy()
+            out["2^%d x %d rows" % (L, batch)] = res
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return out
+
+
 NOMINAL_HBM_GBPS = 8000.0   # GB300 HBM3e, nominal
 
 
@@ -517,6 +571,10 @@ def digest(line):
                 d[k + "_us"] = r(t[k]["us"], 1)
                 if "rel_l2_max" in t[k]:
                     d[k + "_rel_l2_max"] = float("%.2e" % t[k]["rel_l2_max"])
+    sc = line.get("radix_schedules")
+    if sc:
+        for w, res in sc.items():
+            d["sched_" + w.split()[0] + "_us"] = {k: r(v["us"], 1) for k, v in res.items() if k != "autotuned"}
     a = line.get("autograd")
     if a:
         d["autograd_fft_adjoint_us"] = r(a["fft_plus_adjoint_us"], 1)
@@ -750,6 +808,7 @@ def run_moa(args):
     batched = None if args.no_batched else batched_report(torch, moafft, inputs, dev, max(3, min(args.steps, 20)))
     autograd = None if args.no_batched else autograd_report(torch, moafft, inputs, dev, max(3, min(args.steps, 20)))
     small = None if args.no_batched else small_report(torch, moafft, inputs, dev, 200)
+    schedules = None if args.no_batched else schedules_report(torch, moafft, dev, 20, peak)
     tensor_core = None if args.no_batched else tensor_core_report(torch, moafft, inputs, dev, max(3, min(args.steps, 20)),
                                                                   not args.no_oracle)
 
@@ -763,7 +822,7 @@ def run_moa(args):
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "passes_per_step": launches_per_step},
                 "plans": choices, "kernels": kernels, "tensor_core": tensor_core, "batched_uneven": batched, "autograd": autograd,
-                "small_1d": small, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
+                "small_1d": small, "radix_schedules": schedules, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches_per_step * args.steps, "rel_l2": parity or None,
                 "parity_ok": (all(v <= TOL for v in parity.values()) if parity else None),
                 "roofline": roofline, "lifted_1d": lifted}

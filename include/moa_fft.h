@@ -233,7 +233,16 @@ MOA_API moa_status_t moa_fft_batched_queue(const int64_t *lengths, int64_t count
  *   table 1: lo[i] = w_n^i, i < 2^h, and
  *   table 2: hi[j] = w_n^(j * 2^h), j < n / 2^h: the two halves of the
  *            four-step twiddle w_n^e = lo[e mod 2^h] * hi[e / 2^h] of a
- *            lifted 1-D plan of length n (present when the plan lifts).
+ *            lifted 1-D plan of length n (present when the plan lifts);
+ *   table 3, 4: the stage table (layout of table 0) of the 2^index-point
+ *            transform in radix schedule 1 (radix 16 with the small radix
+ *            last) or 2 (radix-8 stages), present when a generic pass of
+ *            the plan runs that schedule (Sec. 4.8: any factorisation of the
+ *            in-register stages gives the same transform; the autotuner, or
+ *            MOA_SCHED, picks one);
+ *   table 5: the table of the warp-shuffle row kernel of 2^index points
+ *            (index 7..9, N = 2^index, T = N/16): rows k = 1, 2, 3, 4, 8, 12
+ *            of w_N^(u*k), u < T, then w_T^u, u < T.
  *   host_out : caller-owned host memory of `capacity` complex64 entries;
  *              NULL with capacity 0 only reports *entries.
  *   entries  : receives the table's length (may be NULL).
@@ -249,7 +258,8 @@ MOA_API moa_status_t moa_fft_plan_table(moa_fft_plan_t plan, int table, int inde
  * 256^3 form for multi-D), the kernel each pass launches and the workspace
  * size, without touching the GPU and without allocating device memory.  The
  * environment overrides the plan reads (MOA_SPLIT_LOG2R, MOA_PIPE,
- * MOA_LIFT3, MOA_3D_TWO_PASS, MOA_TC_KERNEL) apply here too.
+ * MOA_LIFT3, MOA_3D_TWO_PASS, MOA_TC_KERNEL, MOA_SCHED: radix schedule of
+ * the generic passes, 0..3 as in moa_fft_plan_table) apply here too.
  *   n, dims, batch, dtype : as for moa_fft_plan (same checks, same error
  *                           codes; the sign does not change the plan).
  *   tma    : 1 = assume the driver's tensor-map encoder is present (the

@@ -153,17 +153,29 @@ template <> __device__ __forceinline__ void dft<8>(float2 *v) { dft8(v); }
 template <> __device__ __forceinline__ void dft<16>(float2 *v) { dft16(v); }
 
 // ---------------------------------------------------------------------------
-// Radix schedule for N = 2^L: one stage of radix N when L <= 4, otherwise
-// stages of radix 16 preceded by one stage of radix 2^(L mod 4) when L is
-// not a multiple of 4 (the small radix first, so the last stage is always
-// radix 16 and reads contiguous groups of 16 from shared memory).
-template <int LOGN> struct Sched {
+// Radix schedules for N = 2^L (any factorisation is a valid breakpoint,
+// Sec. 4.8; the autotuner picks one by timing).  V selects the schedule:
+//   V = 0: one stage of radix N when L <= 4, otherwise stages of radix 16
+//          preceded by one stage of radix 2^(L mod 4) when L is not a
+//          multiple of 4 (the small radix first, so the last stage reads
+//          contiguous groups of 16 from shared memory);
+//   V = 1: the same radices with the small one last;
+//   V = 2: stages of radix 8, preceded by one of radix 2^(L mod 3) when L is
+//          not a multiple of 3.
+// Every thread holds P = 16 points in every schedule (two butterflies per
+// stage of radix 8, eight of radix 2).
+template <int LOGN, int V = 0> struct Sched {
+    static_assert(V >= 0 && V <= 2, "radix schedules 0, 1, 2");
     static constexpr int N = 1 << LOGN;
     static constexpr int P = N < 16 ? N : 16;          // points per thread
     static constexpr int T = N / P;                    // threads per transform
-    static constexpr int S = LOGN <= 4 ? 1 : (LOGN + 3) / 4;
+    static constexpr int S = V == 2 ? (LOGN <= 3 ? 1 : (LOGN + 2) / 3) : (LOGN <= 4 ? 1 : (LOGN + 3) / 4);
     __host__ __device__ static constexpr int rlog(int s)
     {
+        if (V == 2)
+            return LOGN <= 3 ? LOGN : ((s == 0 && (LOGN % 3) != 0) ? (LOGN % 3) : 3);
+        if (V == 1)
+            return LOGN <= 4 ? LOGN : ((s == S - 1 && (LOGN % 4) != 0) ? (LOGN % 4) : 4);
         return LOGN <= 4 ? LOGN : ((s == 0 && (LOGN % 4) != 0) ? (LOGN % 4) : 4);
     }
     __host__ __device__ static constexpr int K(int s)  // product of earlier radices
@@ -183,7 +195,29 @@ template <int LOGN> struct Sched {
         return o;
     }
     __host__ __device__ static constexpr int tw_entries() { return tw_offset(S - 1); }
+    // The exchanges address element e = w + off as a per-thread base plus a
+    // compile-time offset (Layout below), which needs every stage but the
+    // last to write at offsets N/R * k that are multiples of 16.  (The reads
+    // always qualify: their base mod 16 plus their offset mod 16 stays below
+    // 16 for power-of-two radices.)
+    __host__ __device__ static constexpr bool valid()
+    {
+        if (P != 16 && S > 1)
+            return false;
+        for (int s = 0; s + 1 < S; ++s)
+            if (((N >> rlog(s)) & 15) != 0)
+                return false;
+        return true;
+    }
 };
+
+// Whether schedule V exists for 2^logN points and differs from schedule 0
+// (V = 1 only when L is not a multiple of 4, L >= 9; V = 2 for L >= 7).
+__host__ __device__ constexpr bool sched_variant_ok(int logN, int V)
+{
+    return V == 0 ? (logN >= 1 && logN <= 12)
+                  : V == 1 ? (logN >= 9 && logN <= 11) : V == 2 ? (logN >= 7 && logN <= 12) : false;
+}
 
 // exponent multipliers of the six stored twiddle rows
 __host__ __device__ constexpr int tw_row_k(int j) { return j < 4 ? j + 1 : (j == 4 ? 8 : 12); }
@@ -256,10 +290,10 @@ __device__ __forceinline__ void apply_twiddles(float2 *v, const float2 *__restri
 }
 
 // Element index (within the transform) held in register r before stage 0.
-template <int LOGN>
+template <int LOGN, int V = 0>
 __device__ __forceinline__ int load_index(int r, int tau)
 {
-    using Sc = Sched<LOGN>;
+    using Sc = Sched<LOGN, V>;
     constexpr int R = 1 << Sc::rlog(0);
     constexpr int NB = Sc::P / R;
     return tau + Sc::T * ((r / R) + NB * (r % R));
@@ -268,10 +302,10 @@ __device__ __forceinline__ int load_index(int r, int tau)
 // Radix-R DFTs and twiddles of stage s on the registers of one thread.
 // TWID = false leaves out the twiddles (a 2-D DFT whose slowest axis is the
 // stage-0 digit: the stage-0 DFT is then a transform of its own).
-template <int LOGN, int s, bool TWID = true>
+template <int LOGN, int s, bool TWID = true, int V = 0>
 __device__ __forceinline__ void stage_compute(float2 (&v)[16], int tau, const float2 *__restrict__ tw)
 {
-    using Sc = Sched<LOGN>;
+    using Sc = Sched<LOGN, V>;
     constexpr int R = 1 << Sc::rlog(s);
     constexpr int NB = Sc::P / R;
     constexpr int M1 = Sc::M1(s);
@@ -286,10 +320,10 @@ __device__ __forceinline__ void stage_compute(float2 (&v)[16], int tau, const fl
 }
 
 // Scatter stage s outputs to their Stockham positions in shared memory.
-template <int LOGN, int s, int LAY>
+template <int LOGN, int s, int LAY, int V = 0>
 __device__ __forceinline__ void stage_write(const float2 (&v)[16], float2 *sm, int tau, int f)
 {
-    using Sc = Sched<LOGN>;
+    using Sc = Sched<LOGN, V>;
     using Ly = Layout<Sc::N, LAY>;
     constexpr int R = 1 << Sc::rlog(s);
     constexpr int NB = Sc::P / R;
@@ -308,10 +342,10 @@ __device__ __forceinline__ void stage_write(const float2 (&v)[16], float2 *sm, i
 }
 
 // Gather stage s inputs from shared memory.
-template <int LOGN, int s, int LAY>
+template <int LOGN, int s, int LAY, int V = 0>
 __device__ __forceinline__ void stage_read(float2 (&v)[16], const float2 *sm, int tau, int f)
 {
-    using Sc = Sched<LOGN>;
+    using Sc = Sched<LOGN, V>;
     using Ly = Layout<Sc::N, LAY>;
     constexpr int R = 1 << Sc::rlog(s);
     constexpr int NB = Sc::P / R;
@@ -330,26 +364,47 @@ __device__ __forceinline__ void stage_read(float2 (&v)[16], const float2 *sm, in
 
 // Stages 1..S-1 (stage 0 has been computed by the caller).  Every thread of
 // the block must call this (it contains block barriers).  On return the
-// thread holds outputs X[tau + T*k] in v[k], k < P.
-template <int LOGN, int s, int LAY>
+// thread holds the last stage's outputs: butterfly b = tau + T*i, output k
+// (element X[b + (N/R)*k] for the last radix R) in v[i*R + k].
+template <int LOGN, int s, int LAY, int V = 0>
 __device__ __forceinline__ void run_stages(float2 (&v)[16], float2 *sm, int tau, int f,
                                            const float2 *__restrict__ tw)
 {
-    if constexpr (s < Sched<LOGN>::S) {
-        stage_write<LOGN, s - 1, LAY>(v, sm, tau, f);
+    if constexpr (s < Sched<LOGN, V>::S) {
+        stage_write<LOGN, s - 1, LAY, V>(v, sm, tau, f);
         __syncthreads();
-        stage_read<LOGN, s, LAY>(v, sm, tau, f);
+        stage_read<LOGN, s, LAY, V>(v, sm, tau, f);
         __syncthreads();
-        stage_compute<LOGN, s>(v, tau, tw);
-        run_stages<LOGN, s + 1, LAY>(v, sm, tau, f, tw);
+        stage_compute<LOGN, s, true, V>(v, tau, tw);
+        run_stages<LOGN, s + 1, LAY, V>(v, sm, tau, f, tw);
     }
 }
 
-template <int LOGN, int LAY>
+// The whole transform of the registers v (loaded in the order of
+// load_index).  On return the thread holds X[tau + T*q] in v[q], q < P, in
+// every schedule: when the last radix R is below P, the thread's P/R last
+// butterflies b = tau + T*i give X[tau + T*(i + (P/R)*k)] as output k, and the
+// registers are renamed into that order (a compile-time permutation).
+template <int LOGN, int LAY, int V = 0>
 __device__ __forceinline__ void fft_tile(float2 (&v)[16], float2 *sm, int tau, int f, const float2 *__restrict__ tw)
 {
-    stage_compute<LOGN, 0>(v, tau, tw);
-    run_stages<LOGN, 1, LAY>(v, sm, tau, f, tw);
+    using Sc = Sched<LOGN, V>;
+    static_assert(Sc::valid(), "radix schedule not usable for this length");
+    stage_compute<LOGN, 0, true, V>(v, tau, tw);
+    run_stages<LOGN, 1, LAY, V>(v, sm, tau, f, tw);
+    constexpr int RL = 1 << Sc::rlog(Sc::S - 1);
+    constexpr int NBL = Sc::P / RL;
+    if constexpr (NBL > 1) {
+        float2 t[16];
+#pragma unroll
+        for (int r = 0; r < Sc::P; ++r)
+            t[r] = v[r];
+#pragma unroll
+        for (int i = 0; i < NBL; ++i)
+#pragma unroll
+            for (int k = 0; k < RL; ++k)
+                v[i + NBL * k] = t[i * RL + k];
+    }
 }
 
 // Largest number of transforms per tile of the interleaved layout for

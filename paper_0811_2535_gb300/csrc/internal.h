@@ -64,10 +64,15 @@ struct PassDesc {
     int umma;       // PASS_TC: 1 = tcgen05 kernel (tc_umma.cu), 0 = mma.sync kernel
     int cdiv;       // PASS_COL twiddle: column divisor (0 or 1: none)
     int twlog;      // PASS_COL twiddle: log2 M of its table (0: the plan's main table lo/hi)
+    int sched;      // generic row and column passes: radix schedule V of Sched<logN, V> (0, 1, 2),
+                    // or 3 = row_warp_kernel (natural-order rows of 128..512 points, cross-lane
+                    // stages by warp shuffles)
 };
 
 struct TwiddleSet {
     const float2 *stage[13];   // per logN: stage tables (Sched<logN> layout), or null
+    const float2 *vstage[4][13];   // per schedule V = 1, 2 and logN: stage tables of Sched<logN, V>;
+                                   // vstage[3]: row_warp_kernel's tables (V = 0 uses `stage`)
     const float2 *lo, *hi;     // two-level table of w_n^e: lo[e & (2^h-1)] * hi[e >> h]
     int h;
     const float2 *xlo[32], *xhi[32];   // further two-level tables of w_M, by log2 M (lifted axes)
@@ -145,9 +150,14 @@ int pass_threads(const PassDesc &d);
 // One-time per-process kernel attribute set-up (dynamic shared memory).
 cudaError_t prepare_kernels();
 
-// Twiddle generation (FP64 on the device, rounded once to FP32).
-int stage_table_entries(int logN);
-cudaError_t generate_stage_table(float2 *dst, int logN, cudaStream_t stream);
+// Twiddle generation (FP64 on the device, rounded once to FP32).  Stage
+// tables of schedule V (0, 1, 2: Sched<logN, V>; 3: the warp-shuffle row
+// kernel, rows k = 1, 2, 3, 4, 8, 12 of w_N^(u*k), u < N/16, then w_{N/16}^u);
+// -1 entries for a schedule that does not exist for logN.
+int stage_table_entries(int logN, int V = 0);
+cudaError_t generate_stage_table(float2 *dst, int logN, cudaStream_t stream, int V = 0);
+// whether schedule V (0..3) exists for 2^logN points
+bool sched_exists(int logN, int V);
 // w_n^e for e < 2^h (lo) and w_n^(e*2^h) for e < n/2^h (hi); sign -1.
 cudaError_t generate_two_level(float2 *lo, float2 *hi, int logn, int h, cudaStream_t stream);
 

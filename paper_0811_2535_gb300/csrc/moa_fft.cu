@@ -65,6 +65,7 @@ struct moa_fft_plan_s {
     int opt_3d2 = -1;             // 3-D 256^3: 1 = two passes, 0 = one pass per axis
     std::string how;              // where the choices came from (defaults, autotuner, its cache)
     int opt_lift3 = -1;           // 1-D: 1 = three-level lift (r = 256, fused second/third pass)
+    int opt_sched = -1;           // radix schedule of the generic passes (0..3, see assign_sched)
     bool fault_wait = false;      // MOA_FAULT_WAIT=1 at plan time (tests): short device waits
     bool tma = false;             // tensor-map encoder present: pipelined kernels and the two-pass 3-D plan allowed
     moa::Lift3Launch l3{};
@@ -419,6 +420,29 @@ void assign_pipe(moa_fft_plan_s *p)
     }
 }
 
+// Radix schedule of every generic row and column pass (the pipelined and
+// fused kernels keep their own): 0 = small radix first, 1 = small radix
+// last, 2 = radix-8 stages (Sched<logN, V> in fft_core.cuh), 3 = the
+// warp-shuffle row kernel for natural-order rows of 128..512 points.  A pass
+// for which the chosen schedule does not exist keeps schedule 0.  The
+// autotuner's choice, else MOA_SCHED, else 0.
+void assign_sched(moa_fft_plan_s *p)
+{
+    const int want = p->opt_sched >= 0 ? p->opt_sched : env_int("MOA_SCHED", 0);
+    for (PassDesc &d : p->passes) {
+        d.sched = 0;
+        if (d.pipe || (d.kind != moa::PASS_ROW && d.kind != moa::PASS_COL) || want <= 0 || want > 3)
+            continue;
+        if (!moa::sched_exists(d.logN, want))
+            continue;
+        // the warp-shuffle kernel: natural-order rows, blocks of 1 to 8 whole warps
+        const int threads = moa::pass_threads(d);
+        if (want == 3 && (d.kind != moa::PASS_ROW || d.Rt > 1 || threads % 32 != 0 || threads > 256))
+            continue;
+        d.sched = want;
+    }
+}
+
 // Device block of the fused second/third pass of a three-level lift: the
 // two-level table of w_c (c = cA cB), the ticket and two counters per unit
 // (the queue itself is decoded from the ticket), then a ring of four units
@@ -517,6 +541,16 @@ moa_status_t allocate_and_fill(moa_fft_plan_s *p)
             bytes += ((size_t)ent * sizeof(float2) + 255) & ~size_t(255);
         }
     }
+    // tables of the other radix schedules used by the generic passes
+    size_t voffs[4][13] = {{0}};
+    for (const PassDesc &d : p->passes)
+        if (d.sched > 0 && !voffs[d.sched][d.logN]) {
+            const int ent = moa::stage_table_entries(d.logN, d.sched);
+            if (ent <= 0)
+                return MOA_ERR_INVALID_ARG;
+            voffs[d.sched][d.logN] = bytes;
+            bytes += ((size_t)ent * sizeof(float2) + 255) & ~size_t(255);
+        }
     size_t lo_off = 0, hi_off = 0;
     int logn = 0, h = 0;
     if (p->split_r > 0) {
@@ -572,6 +606,15 @@ moa_status_t allocate_and_fill(moa_fft_plan_s *p)
             p->tw.stage[l] = reinterpret_cast<float2 *>(base + offs[l]);
             if (moa::generate_stage_table(const_cast<float2 *>(p->tw.stage[l]), l, 0) != cudaSuccess)
                 return MOA_ERR_CUDA;
+        }
+        for (int v = 0; v < 4; ++v) {
+            p->tw.vstage[v][l] = nullptr;
+            if (v > 0 && voffs[v][l]) {
+                float2 *t = reinterpret_cast<float2 *>(base + voffs[v][l]);
+                if (moa::generate_stage_table(t, l, 0, v) != cudaSuccess)
+                    return MOA_ERR_CUDA;
+                p->tw.vstage[v][l] = t;
+            }
         }
     }
     if (tc_off) {
@@ -1097,8 +1140,14 @@ void pass_name(const moa_fft_plan_s *p, const PassDesc &d, char *buf, size_t len
         snprintf(buf, len, "pipe_col_kernel<%d,%d,%d>", d.logN, d.tw4, d.blk);
     else if (d.pipe)
         snprintf(buf, len, "pipe_rowT_kernel<%d>", d.logN);
+    else if (d.sched == 3)
+        snprintf(buf, len, "row_warp_kernel<%d>", d.logN);
+    else if (d.kind == moa::PASS_COL && d.sched > 0)
+        snprintf(buf, len, "col_pass_kernel<%d,%d,%d>", d.logN, d.tw4, d.sched);
     else if (d.kind == moa::PASS_COL)
         snprintf(buf, len, "col_pass_kernel<%d,%d>", d.logN, d.tw4);
+    else if (d.sched > 0)
+        snprintf(buf, len, "row_pass_kernel<%d,%d,%d>", d.logN, d.Rt > 1 ? 1 : 0, d.sched);
     else
         snprintf(buf, len, "row_pass_kernel<%d,%d>", d.logN, d.Rt > 1 ? 1 : 0);
 }
@@ -1133,7 +1182,7 @@ void log_plan(const moa_fft_plan_s *p, const char *how)
 // Choices a plan may have fixed (the autotuner's candidates); -1 = default
 // or environment override.
 struct PlanOpts {
-    int lr = -1, pipe = -1, lift3 = -1, tile = -1, two_pass3d = -1;
+    int lr = -1, pipe = -1, lift3 = -1, tile = -1, two_pass3d = -1, sched = -1;
 };
 
 moa_status_t make_plan(moa_fft_plan_s **out, const int64_t *n, int dims, int64_t batch, int sign, int dtype,
@@ -1155,11 +1204,13 @@ moa_status_t make_plan(moa_fft_plan_s **out, const int64_t *n, int dims, int64_t
     p->opt_lift3 = o.lift3;
     p->opt_tile = o.tile;
     p->opt_3d2 = o.two_pass3d;
+    p->opt_sched = o.sched;
     p->tma = moa::pipe_supported();
     p->fault_wait = env_int("MOA_FAULT_WAIT", 0) == 1;
     moa_status_t st = build_passes(p);
     if (st == MOA_OK) {
         assign_pipe(p);
+        assign_sched(p);
         st = allocate_and_fill(p);
     }
     if (st != MOA_OK) {
@@ -1266,7 +1317,9 @@ moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int6
     // made by timing, as the paper's script-based search does): every
     // admissible r x c split of a lifted 1-D transform and its three-level
     // lift, the pipelined or generic strided kernels, the tile size of the
-    // generic passes, and for 256^3 arrays the two-pass or per-axis form.
+    // generic passes, and for 256^3 arrays the two-pass or per-axis form;
+    // then, on the best of those, the radix schedule of the generic passes
+    // (small radix first or last, radix-8 stages, warp-shuffle rows).
     // Candidates that build the same passes are timed once.  A choice fixed
     // by an environment override is not searched.
     PlanOpts best_opts;
@@ -1281,13 +1334,14 @@ moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int6
         for (int i = 0; i < dims; ++i)
             key += ":" + std::to_string((long long)n[i]);
         key += ":" + std::to_string((long long)batch) + ":";
-        const char *fixed[] = {"MOA_SPLIT_LOG2R", "MOA_LIFT3", "MOA_PIPE", "MOA_TILE_LOG2", "MOA_3D_TWO_PASS"};
-        for (int i = 0; i < 5; ++i)
+        const char *fixed[] = {"MOA_SPLIT_LOG2R", "MOA_LIFT3", "MOA_PIPE", "MOA_TILE_LOG2", "MOA_3D_TWO_PASS",
+                               "MOA_SCHED"};
+        for (int i = 0; i < 6; ++i)
             key += env_set(fixed[i]) ? "f" : "s";
         std::string v;
         PlanOpts c;
-        if (tune_get(key, v) && sscanf(v.c_str(), "%d %d %d %d %d", &c.lr, &c.pipe, &c.lift3, &c.tile,
-                                       &c.two_pass3d) == 5) {
+        if (tune_get(key, v) && sscanf(v.c_str(), "%d %d %d %d %d %d", &c.lr, &c.pipe, &c.lift3, &c.tile,
+                                       &c.two_pass3d, &c.sched) == 6) {
             best_opts = c;
             how = "autotuner choice from the cache";
         } else {
@@ -1327,18 +1381,22 @@ moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int6
                 }
             float best = INFINITY;
             std::set<std::string> seen;
-            for (const PlanOpts &o : cands) {
+            // time one candidate (once per distinct pass list); false on a hard error
+            moa_status_t err = MOA_OK;
+            auto consider = [&](const PlanOpts &o) {
                 moa_fft_plan_s *cand = nullptr;
                 const moa_status_t st = make_plan(&cand, n, dims, batch, sign, dtype, total, o);
                 if (st == MOA_ERR_UNSUPPORTED)
-                    continue;
-                if (st != MOA_OK)
-                    return st;
+                    return true;
+                if (st != MOA_OK) {
+                    err = st;
+                    return false;
+                }
                 const std::string sig = plan_signature(cand);
                 if (!seen.insert(sig).second) {   // the same passes as a candidate already timed
                     free_plan_memory(cand);
                     delete cand;
-                    continue;
+                    return true;
                 }
                 const float ms = time_exec(cand);
                 if (log_enabled())
@@ -1349,11 +1407,27 @@ moa_status_t moa_fft_plan(moa_fft_plan_t *plan, const int64_t *n, int dims, int6
                     best = ms;
                     best_opts = o;
                 }
+                return true;
+            };
+            for (const PlanOpts &o : cands)
+                if (!consider(o))
+                    return err;
+            // then the radix schedule of the generic passes, on the best plan
+            // (schedules that change no pass give the same pass list and are
+            // not timed again)
+            if (!env_set("MOA_SCHED") && std::isfinite(best)) {
+                const PlanOpts base = best_opts;
+                for (int sc = 1; sc <= 3; ++sc) {
+                    PlanOpts o = base;
+                    o.sched = sc;
+                    if (!consider(o))
+                        return err;
+                }
             }
             if (std::isfinite(best))
                 tune_put(key, std::to_string(best_opts.lr) + " " + std::to_string(best_opts.pipe) + " " +
                                   std::to_string(best_opts.lift3) + " " + std::to_string(best_opts.tile) + " " +
-                                  std::to_string(best_opts.two_pass3d));
+                                  std::to_string(best_opts.two_pass3d) + " " + std::to_string(best_opts.sched));
         }
     }
     moa_fft_plan_s *p = nullptr;
@@ -1643,6 +1717,12 @@ moa_status_t moa_fft_plan_table(moa_fft_plan_t plan, int table, int index, void 
             return MOA_ERR_INVALID_ARG;
         src = plan->tw.stage[index];
         count = moa::stage_table_entries(index);
+    } else if (table >= 3 && table <= 5) {
+        const int v = table - 2;
+        if (index < 1 || index > 12 || !plan->tw.vstage[v][index])
+            return MOA_ERR_INVALID_ARG;
+        src = plan->tw.vstage[v][index];
+        count = moa::stage_table_entries(index, v);
     } else if (table == 1 || table == 2) {
         if (!plan->tw.lo || !plan->tw.hi)
             return MOA_ERR_INVALID_ARG;
@@ -1683,6 +1763,7 @@ moa_status_t moa_fft_estimate(const int64_t *n, int dims, int64_t batch, int dty
     if (const moa_status_t st = build_passes(&p))
         return st;
     assign_pipe(&p);
+    assign_sched(&p);
     if (passes)
         *passes = (int)p.passes.size();
     if (split_r)

@@ -24,14 +24,14 @@ __device__ __forceinline__ float2 two_level(const float2 *__restrict__ lo, const
     return cmul(__ldg(&lo[e & ((int64_t(1) << h) - 1)]), __ldg(&hi[e >> h]));
 }
 
-template <int LOGN, bool TW4>
+template <int LOGN, bool TW4, int V = 0>
 __global__ void __launch_bounds__(1024) col_pass_kernel(const float2 *in, float2 *out, int C, int logF,
                                                         int logTpo, const float2 *__restrict__ tw,
                                                         const float2 *__restrict__ tw_lo,
                                                         const float2 *__restrict__ tw_hi, int tw_h, int flags,
                                                         int Rt, int log_cdiv)
 {
-    using Sc = Sched<LOGN>;
+    using Sc = Sched<LOGN, V>;
     extern __shared__ float2 smem[];
     const int F = 1 << logF;
     const int tid = threadIdx.x;
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(1024) col_pass_kernel(const float2 *in, float2
             tk[(k << LAY) + f] = two_level(tw_lo, tw_hi, tw_h, tcol * ((int64_t)Rt * Sc::T * k));
     }
 
-    fft_tile<LOGN, LAY>(v, smem, tau, f, tw);
+    fft_tile<LOGN, LAY, V>(v, smem, tau, f, tw);
 
     if constexpr (TW4) {
         const float2 A = two_level(tw_lo, tw_hi, tw_h, tcol * (orow + (int64_t)Rt * tau));
@@ -100,11 +100,11 @@ __global__ void __launch_bounds__(1024) col_pass_kernel(const float2 *in, float2
     pdl_launch_dependents();   // after the stores: the next kernel launches as the last blocks finish
 }
 
-template <int LOGN, bool TRANS>
+template <int LOGN, bool TRANS, int V = 0>
 __global__ void __launch_bounds__(1024) row_pass_kernel(const float2 *in, float2 *out, int64_t O, int64_t Rt,
                                                         int logF, const float2 *__restrict__ tw, int flags)
 {
-    using Sc = Sched<LOGN>;
+    using Sc = Sched<LOGN, V>;
     extern __shared__ float2 smem[];
     const int F = 1 << logF;
     const int tid = threadIdx.x;
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(const float2 *in, float2
             v[r].y = -v[r].y;
     }
 
-    fft_tile<LOGN, LAY>(v, smem, tau, f, tw);
+    fft_tile<LOGN, LAY, V>(v, smem, tau, f, tw);
 
     if (flags & FLAG_CONJ_OUT) {
 #pragma unroll
@@ -151,6 +151,92 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(const float2 *in, float2
 #pragma unroll
         for (int k = 0; k < Sc::P; ++k)
             dst[k * step] = v[k];
+    }
+    pdl_launch_dependents();
+}
+
+// Row pass (natural order) for N = 128, 256, 512 with the butterflies that
+// cross lanes done by warp shuffles: no shared-memory exchange between the
+// radix stages and no block barrier.  N = 16 * T, element j = lam + T*q of a
+// transform in lane lam (< T) of its group of T lanes, register q:
+//   1. a radix-16 DFT over q in registers (outputs k1), then the twiddle
+//      w_N^(lam*k1) (the first step of the lifting n = 16 x T, Sec. 4.2);
+//   2. the T-point DFTs over lam as log2 T radix-2 stages across lanes
+//      (decimation in frequency, Sec. 3.5-3.6's butterfly on lane pairs
+//      lam, lam ^ h): each lane sends its value with shfl.xor, the lower lane
+//      keeps the sum, the upper one the difference times w_2h^(lam mod h);
+//      the lane then holds k2 = bitrev(lam), i.e. X[k1 + 16*bitrev(lam)];
+//   3. the warp's outputs (32/T transforms, 512 complex64 contiguous in
+//      memory) pass through a warp-private staging area (row = lane, 17
+//      entries a row: conflict-free both ways) behind __syncwarp, so every
+//      store instruction writes 256 contiguous bytes.
+// Each block holds T << logF threads, a multiple of 32 up to 256 (the plan
+// uses this kernel only then), so every shuffle has its whole warp.  `tw` holds rows
+// k = 1, 2, 3, 4, 8, 12 of w_N^(u*k), u < T, then w_T^u, u < T.
+template <int LOGN>
+__global__ void __launch_bounds__(256) row_warp_kernel(const float2 *in, float2 *out, int64_t O, int logF,
+                                                       const float2 *__restrict__ tw, int flags)
+{
+    constexpr int N = 1 << LOGN, T = N / 16, LT = LOGN - 4;
+    static_assert(T >= 8 && T <= 32, "N = 128, 256, 512");
+    extern __shared__ float2 smem[];
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int lam = lane & (T - 1), g = lane >> LT;
+    const int64_t o0 = ((int64_t)blockIdx.x << logF) + (int64_t)warp * (32 / T);   // the warp's first row
+    const int64_t o = o0 + g;
+    pdl_wait_prior();   // `in` may be the previous kernel's output, `out` its input
+    float2 v[16];
+    if (o < O) {
+        const float2 *src = in + o * N + lam;
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            v[q] = src[q * T];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            v[q] = make_float2(0.f, 0.f);
+    }
+    if (flags & FLAG_CONJ_IN) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            v[q].y = -v[q].y;
+    }
+    dft16(v);
+    apply_twiddles<16>(v, tw, lam, T);
+    const float2 *wT = tw + 6 * T;   // w_T^u
+#pragma unroll
+    for (int h = T / 2; h >= 1; h >>= 1) {
+        const bool upper = (lam & h) != 0;
+        const float sg = upper ? -1.f : 1.f;
+        // w_2h^(lam mod h) = w_T^((lam mod h) * T / 2h) on the upper lane, 1 on the lower
+        const float2 w = upper ? __ldg(&wT[(lam & (h - 1)) * (T / (2 * h))]) : make_float2(1.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float px = __shfl_xor_sync(0xffffffffu, v[k].x, h);
+            const float py = __shfl_xor_sync(0xffffffffu, v[k].y, h);
+            // lower: mine + partner; upper: partner - mine
+            v[k] = cmul(make_float2(fmaf(sg, v[k].x, px), fmaf(sg, v[k].y, py)), w);
+        }
+    }
+    if (flags & FLAG_CONJ_OUT) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            v[k].y = -v[k].y;
+    }
+    float2 *stg = smem + warp * (32 * 17);
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+        stg[lane * 17 + k] = v[k];
+    __syncwarp();
+    float2 *dst = out + o0 * N;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        const int p = lane + 32 * m;            // position in the warp's 32 x 16 outputs
+        const int fl = p >> LOGN, k = p & (N - 1);
+        const int row = fl * T + (int)(__brev((unsigned)(k >> 4)) >> (32 - LT));
+        if (o0 + fl < O)
+            dst[p] = stg[row * 17 + (k & 15)];
     }
     pdl_launch_dependents();
 }
@@ -212,12 +298,13 @@ __global__ void __launch_bounds__(256, 5) plane3d_p1_kernel(const float2 *in, fl
     pdl_launch_dependents();   // after the stores
 }
 
-template <int LOGN>
-cudaError_t launch_typed(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
-                         cudaStream_t stream)
+template <int LOGN, int V>
+cudaError_t launch_typed_v(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
+                           cudaStream_t stream)
 {
     const int threads = pass_threads(d);
     const size_t smem = pass_smem_bytes(d);
+    const float2 *stage = V == 0 ? tw.stage[LOGN] : tw.vstage[V][LOGN];
     if (d.kind == PASS_COL) {
         int logTpo = 0;
         while ((int64_t(1) << logTpo) < (d.C >> d.logF))
@@ -227,33 +314,77 @@ cudaError_t launch_typed(const PassDesc &d, const float2 *in, float2 *out, const
         while ((1 << log_cdiv) < d.cdiv)
             ++log_cdiv;
         const bool xt = d.twlog > 0;   // a further table (a lifted axis) instead of the main one
-        return launch_maybe_dependent(d.tw4 ? col_pass_kernel<LOGN, true> : col_pass_kernel<LOGN, false>,
+        return launch_maybe_dependent(d.tw4 ? col_pass_kernel<LOGN, true, V> : col_pass_kernel<LOGN, false, V>,
                                       (unsigned)grid, threads, smem, stream, flags & FLAG_PDL, in, out, (int)d.C,
-                                      d.logF, logTpo, tw.stage[LOGN], xt ? tw.xlo[d.twlog] : tw.lo,
+                                      d.logF, logTpo, stage, xt ? tw.xlo[d.twlog] : tw.lo,
                                       xt ? tw.xhi[d.twlog] : tw.hi, xt ? tw.xh[d.twlog] : tw.h, flags,
                                       (int)(d.Rt > 1 ? d.Rt : 1), log_cdiv);
     }
     const int64_t grid = (d.O + (int64_t(1) << d.logF) - 1) >> d.logF;
-    return launch_maybe_dependent(d.Rt > 1 ? row_pass_kernel<LOGN, true> : row_pass_kernel<LOGN, false>,
+    return launch_maybe_dependent(d.Rt > 1 ? row_pass_kernel<LOGN, true, V> : row_pass_kernel<LOGN, false, V>,
                                   (unsigned)grid, threads, smem, stream, flags & FLAG_PDL, in, out, d.O, d.Rt,
-                                  d.logF, tw.stage[LOGN], flags);
+                                  d.logF, stage, flags);
+}
+
+template <int LOGN>
+cudaError_t launch_typed(const PassDesc &d, const float2 *in, float2 *out, const TwiddleSet &tw, int flags,
+                         cudaStream_t stream)
+{
+    if constexpr (LOGN >= 7 && LOGN <= 9) {
+        if (d.sched == 3) {
+            if (d.kind != PASS_ROW || d.Rt > 1 || pass_threads(d) % 32 != 0 || pass_threads(d) > 256 ||
+                !tw.vstage[3][LOGN])
+                return cudaErrorInvalidValue;
+            const int64_t grid = (d.O + (int64_t(1) << d.logF) - 1) >> d.logF;
+            return launch_maybe_dependent(row_warp_kernel<LOGN>, (unsigned)grid, pass_threads(d),
+                                          pass_smem_bytes(d), stream, flags & FLAG_PDL, in, out, d.O, d.logF,
+                                          tw.vstage[3][LOGN], flags);
+        }
+    }
+    if constexpr (sched_variant_ok(LOGN, 1)) {
+        if (d.sched == 1)
+            return launch_typed_v<LOGN, 1>(d, in, out, tw, flags, stream);
+    }
+    if constexpr (sched_variant_ok(LOGN, 2)) {
+        if (d.sched == 2)
+            return launch_typed_v<LOGN, 2>(d, in, out, tw, flags, stream);
+    }
+    if (d.sched != 0)
+        return cudaErrorInvalidValue;
+    return launch_typed_v<LOGN, 0>(d, in, out, tw, flags, stream);
+}
+
+template <int LOGN, int V>
+cudaError_t set_attrs_v()
+{
+    const int max_smem = 227 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(col_pass_kernel<LOGN, true, V>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaFuncSetAttribute(col_pass_kernel<LOGN, false, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             max_smem);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaFuncSetAttribute(row_pass_kernel<LOGN, true, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             max_smem);
+    if (e != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(row_pass_kernel<LOGN, false, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                max_smem);
 }
 
 template <int LOGN>
 cudaError_t set_attrs()
 {
-    const int max_smem = 227 * 1024;
-    cudaError_t e = cudaFuncSetAttribute(col_pass_kernel<LOGN, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    if (e != cudaSuccess)
-        return e;
-    e = cudaFuncSetAttribute(col_pass_kernel<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    if (e != cudaSuccess)
-        return e;
-    e = cudaFuncSetAttribute(row_pass_kernel<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    if (e != cudaSuccess)
-        return e;
-    return cudaFuncSetAttribute(row_pass_kernel<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    cudaError_t e = set_attrs_v<LOGN, 0>();
+    if constexpr (sched_variant_ok(LOGN, 1))
+        if (e == cudaSuccess)
+            e = set_attrs_v<LOGN, 1>();
+    if constexpr (sched_variant_ok(LOGN, 2))
+        if (e == cudaSuccess)
+            e = set_attrs_v<LOGN, 2>();
+    return e;
 }
 
 }  // namespace
@@ -275,6 +406,8 @@ int pass_threads(const PassDesc &d)
 
 size_t pass_smem_bytes(const PassDesc &d)
 {
+    if (d.sched == 3)   // row_warp_kernel: 17 entries per lane of staged outputs
+        return (size_t)pass_threads(d) * 17 * sizeof(float2);
     const int N = 1 << d.logN;
     const int P = N < 16 ? N : 16;
     const size_t F = size_t(1) << d.logF;

@@ -55,60 +55,104 @@ __global__ void full_stage_kernel(float2 *dst, int64_t M, int64_t M1)
     dst[idx] = make_float2((float)c, (float)(-s));
 }
 
-template <int LOGN>
-int entries_typed() { return Sched<LOGN>::tw_entries(); }
+template <int LOGN, int V>
+int entries_typed()
+{
+    if constexpr (V == 3)
+        return 7 * ((1 << LOGN) / 16);
+    else
+        return Sched<LOGN, V>::tw_entries();
+}
 
-template <int LOGN>
+template <int LOGN, int V>
 cudaError_t gen_typed(float2 *dst, cudaStream_t stream)
 {
-    using Sc = Sched<LOGN>;
-    const int total = Sc::tw_entries();
+    StageGen g[3] = {{1, 1, 0}, {1, 1, 0}, {1, 1, 0}};
+    int nst = 0, total = 0;
+    if constexpr (V == 3) {
+        // rows of w_N^(u*k), u < T, then one row of w_T^u
+        constexpr int N = 1 << LOGN, T = N / 16;
+        g[0] = StageGen{N, T, 0};
+        g[1] = StageGen{T, T, 6 * T};
+        nst = 2;
+        total = 7 * T;
+    } else {
+        using Sc = Sched<LOGN, V>;
+        total = Sc::tw_entries();
+        nst = Sc::S - 1;
+        for (int s = 0; s < nst; ++s)
+            g[s] = StageGen{Sc::M1(s) << Sc::rlog(s), Sc::M1(s), Sc::tw_offset(s)};
+    }
     if (total == 0)
         return cudaSuccess;
-    StageGen g[3] = {{1, 1, 0}, {1, 1, 0}, {1, 1, 0}};
-    const int nst = Sc::S - 1;
-    for (int s = 0; s < nst; ++s)
-        g[s] = StageGen{Sc::M1(s) << Sc::rlog(s), Sc::M1(s), Sc::tw_offset(s)};
     stage_table_kernel<<<(total + 255) / 256, 256, 0, stream>>>(dst, total, g[0], g[1], g[2], nst);
     return cudaGetLastError();
 }
 
-}  // namespace
+constexpr bool exists(int logN, int V) { return V == 3 ? (logN >= 7 && logN <= 9) : sched_variant_ok(logN, V); }
 
-int stage_table_entries(int logN)
+template <int LOGN>
+int entries_any(int V)
 {
-    switch (logN) {
-    case 1: return entries_typed<1>();
-    case 2: return entries_typed<2>();
-    case 3: return entries_typed<3>();
-    case 4: return entries_typed<4>();
-    case 5: return entries_typed<5>();
-    case 6: return entries_typed<6>();
-    case 7: return entries_typed<7>();
-    case 8: return entries_typed<8>();
-    case 9: return entries_typed<9>();
-    case 10: return entries_typed<10>();
-    case 11: return entries_typed<11>();
-    case 12: return entries_typed<12>();
+    switch (V) {
+    case 0: return entries_typed<LOGN, 0>();
+    case 1: if constexpr (exists(LOGN, 1)) return entries_typed<LOGN, 1>(); else return -1;
+    case 2: if constexpr (exists(LOGN, 2)) return entries_typed<LOGN, 2>(); else return -1;
+    case 3: if constexpr (exists(LOGN, 3)) return entries_typed<LOGN, 3>(); else return -1;
     default: return -1;
     }
 }
 
-cudaError_t generate_stage_table(float2 *dst, int logN, cudaStream_t stream)
+template <int LOGN>
+cudaError_t gen_any(float2 *dst, int V, cudaStream_t stream)
+{
+    switch (V) {
+    case 0: return gen_typed<LOGN, 0>(dst, stream);
+    case 1: if constexpr (exists(LOGN, 1)) return gen_typed<LOGN, 1>(dst, stream); else return cudaErrorInvalidValue;
+    case 2: if constexpr (exists(LOGN, 2)) return gen_typed<LOGN, 2>(dst, stream); else return cudaErrorInvalidValue;
+    case 3: if constexpr (exists(LOGN, 3)) return gen_typed<LOGN, 3>(dst, stream); else return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+bool sched_exists(int logN, int V) { return V >= 0 && V <= 3 && exists(logN, V); }
+
+int stage_table_entries(int logN, int V)
 {
     switch (logN) {
-    case 1: return gen_typed<1>(dst, stream);
-    case 2: return gen_typed<2>(dst, stream);
-    case 3: return gen_typed<3>(dst, stream);
-    case 4: return gen_typed<4>(dst, stream);
-    case 5: return gen_typed<5>(dst, stream);
-    case 6: return gen_typed<6>(dst, stream);
-    case 7: return gen_typed<7>(dst, stream);
-    case 8: return gen_typed<8>(dst, stream);
-    case 9: return gen_typed<9>(dst, stream);
-    case 10: return gen_typed<10>(dst, stream);
-    case 11: return gen_typed<11>(dst, stream);
-    case 12: return gen_typed<12>(dst, stream);
+    case 1: return entries_any<1>(V);
+    case 2: return entries_any<2>(V);
+    case 3: return entries_any<3>(V);
+    case 4: return entries_any<4>(V);
+    case 5: return entries_any<5>(V);
+    case 6: return entries_any<6>(V);
+    case 7: return entries_any<7>(V);
+    case 8: return entries_any<8>(V);
+    case 9: return entries_any<9>(V);
+    case 10: return entries_any<10>(V);
+    case 11: return entries_any<11>(V);
+    case 12: return entries_any<12>(V);
+    default: return -1;
+    }
+}
+
+cudaError_t generate_stage_table(float2 *dst, int logN, cudaStream_t stream, int V)
+{
+    switch (logN) {
+    case 1: return gen_any<1>(dst, V, stream);
+    case 2: return gen_any<2>(dst, V, stream);
+    case 3: return gen_any<3>(dst, V, stream);
+    case 4: return gen_any<4>(dst, V, stream);
+    case 5: return gen_any<5>(dst, V, stream);
+    case 6: return gen_any<6>(dst, V, stream);
+    case 7: return gen_any<7>(dst, V, stream);
+    case 8: return gen_any<8>(dst, V, stream);
+    case 9: return gen_any<9>(dst, V, stream);
+    case 10: return gen_any<10>(dst, V, stream);
+    case 11: return gen_any<11>(dst, V, stream);
+    case 12: return gen_any<12>(dst, V, stream);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -211,8 +211,9 @@ class Plan:
 
     def table(self, which: int, index: int = 0):
         """Copy of twiddle table ``which`` (0: stage table of 2^index points,
-        1 / 2: low / high half of the four-step twiddle) as a complex64 numpy
-        array (``moa_fft_plan_table``)."""
+        1 / 2: low / high half of the four-step twiddle, 3 / 4 / 5: stage
+        table of radix schedule 1 / 2 / 3 for 2^index points) as a complex64
+        numpy array (``moa_fft_plan_table``)."""
         import numpy as np
         count = _I64()
         _check(lib().moa_fft_plan_table(self._h, int(which), int(index), None, 0, ctypes.byref(count)),

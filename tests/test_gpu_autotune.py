@@ -42,12 +42,12 @@ def test_autotuned_split_is_cached_and_correct(env, tmp_path, monkeypatch):
     t_first = time.perf_counter() - t0
     info = plan.info()
     text = cache.read_text()
-    line = [ln for ln in text.splitlines() if ":plan:1:524288:3:sssss " in ln]
+    line = [ln for ln in text.splitlines() if ":plan:1:524288:3:ssssss " in ln]
     assert len(line) == 1, text
-    lr, pipe, lift3, tile, two = (int(v) for v in line[0].split()[1:6])
+    lr, pipe, lift3, tile, two, sched = (int(v) for v in line[0].split()[1:7])
     assert lift3 == 0          # the three-level lift is a candidate from 2^21 on
     assert info["split_r"] == 1 << lr and 7 <= lr <= 12
-    assert tile in (11, 12, 13) and two == -1
+    assert tile in (11, 12, 13) and two == -1 and sched in (-1, 1, 2, 3)
     assert "autotuned" in plan.choice() and ("r=%d" % (1 << lr)) in plan.choice()
     x = inputs.uniform((3, n), 77)
     y = plan.exec(torch.from_numpy(x).cuda()).cpu().numpy()
@@ -162,3 +162,34 @@ def test_estimate_matches_the_plan(env, shape, batch, dtype, monkeypatch):
     assert e["kernels"] == kernels
     assert (e["passes"], e["split_r"], e["split_c"], e["workspace_bytes"]) == \
         (info["passes"], info["split_r"], info["split_c"], info["workspace_bytes"])
+
+
+@pytest.mark.parametrize("L,batch", [(9, 4096), (11, 1024)])
+def test_autotuner_times_radix_schedules(env, tmp_path, monkeypatch, capfd, L, batch):
+    """The search covers the radix schedule of the generic passes (Sec. 4.8:
+    any factorisation of the in-register stages): small radix first or last,
+    radix-8 stages, and for 2^7..2^9-point rows the warp-shuffle kernel.
+    MOA_LOG=1 lists every timed candidate; the plan kept matches the oracle."""
+    torch, moafft, oracle = env
+    from paper_0811_2535_gb300 import inputs
+    monkeypatch.setenv("MOA_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    monkeypatch.setenv("MOA_AUTOTUNE", "1")
+    monkeypatch.setenv("MOA_LOG", "1")
+    for k in ("MOA_SCHED", "MOA_PIPE"):
+        monkeypatch.delenv(k, raising=False)
+    monkeypatch.setenv("MOA_TILE_LOG2", "12")   # 256-thread blocks, which the warp-shuffle kernel takes
+    n = 1 << L
+    plan = moafft.Plan([n], batch, -1)
+    err_text = capfd.readouterr().err
+    timed = [ln for ln in err_text.splitlines() if "autotune candidate" in ln]
+    want = [f"row_pass_kernel<{L},0>", f"row_pass_kernel<{L},0,1>", f"row_pass_kernel<{L},0,2>"]
+    if L <= 9:
+        want.append(f"row_warp_kernel<{L}>")
+    for w in want:
+        assert any(w + "/" in ln for ln in timed), (w, timed)
+    x = inputs.uniform((batch, n), 90 + L)
+    y = plan.exec(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = oracle.fft_radix2(x.astype(np.complex128), -1)
+    err = np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= TOL
+    plan.destroy()

@@ -179,3 +179,32 @@ def test_four_column_kernel_on_request():
     assert res.returncode == 0, res.stderr
     assert res.stdout.strip() == ("['pipe_col_kernel<12,1,1>', 'pipe_col_kernel<12,0,2>'] "
                                   "['plane3d_p1_kernel', 'pipe_col_kernel<12,0,3>']")
+
+
+@pytest.mark.parametrize("v", [1, 2, 3])
+def test_radix_schedule_override(mf, v, monkeypatch):
+    """MOA_SCHED picks the radix schedule of the generic passes (Sec. 4.8:
+    any factorisation of the in-register stages): 1 = small radix last
+    (2^9..2^11), 2 = radix-8 stages (2^7..2^12), 3 = the warp-shuffle kernel
+    for natural-order rows of 2^7..2^9 points whose blocks are whole warps.
+    A pass for which the schedule does not exist, and every pipelined or
+    fused pass, keeps its own."""
+    monkeypatch.setenv("MOA_SCHED", str(v))
+    ok = {1: range(9, 12), 2: range(7, 13), 3: range(7, 10)}[v]
+    for L in range(1, 13):
+        for batch in (1, 64):
+            k = mf.estimate([1 << L], batch, tma=TMA)["kernels"]
+            threads = (1 << max(L - 4, 0)) << min(12 - L, (batch - 1).bit_length()) if L <= 12 else 0
+            if L in ok and (v != 3 or threads % 32 == 0):
+                assert k == [f"row_warp_kernel<{L}>" if v == 3 else f"row_pass_kernel<{L},0,{v}>"], (L, batch)
+            else:
+                assert k == [f"row_pass_kernel<{L},0>"], (L, batch)
+    # the pipelined N = 4096 passes and the two-pass 3-D form keep their kernels
+    assert mf.estimate([1 << 24], tma=TMA)["kernels"] == ["pipe_col2_kernel<1,1>", "pipe_col2_kernel<0,2>"]
+    assert mf.estimate([256, 256, 256], tma=TMA)["kernels"] == ["plane3d_p1_kernel", "pipe_col2_kernel<0,3>"]
+    # generic lifted passes: column pass with the twiddle and transposed rows
+    k = mf.estimate([1 << 18], tma=NO_TMA)["kernels"]
+    if v == 3:   # transposed rows and column passes keep schedule 0
+        assert k == ["col_pass_kernel<9,1>", "row_pass_kernel<9,1>"]
+    else:
+        assert k == [f"col_pass_kernel<9,1,{v}>", f"row_pass_kernel<9,1,{v}>"]
