@@ -173,3 +173,97 @@ def test_schedule_tables_correctly_rounded(env, sched, v, L):
     ref = schedule_table(L, v)
     assert t.shape == ref.shape
     assert ulps(t, ref).max() <= 1
+
+
+@pytest.mark.parametrize("v,shape,batch", [(1, (2048,), 100), (2, (4096,), 50), (3, (256,), 300), (3, (512,), 64),
+                                           (2, (1 << 18,), 3)])
+def test_schedule_adjoint_and_round_trip(env, sched, v, shape, batch):
+    """The adjoint (opposite-sign, unnormalised) transform on the same plan,
+    against the oracle's +1 transform, and exec then adjoint = n * x."""
+    torch, moafft, oracle = env
+    from paper_0811_2535_gb300 import inputs
+    sched(v, pipe=0)
+    x = inputs.uniform((batch,) + shape, 8500 + v + batch)
+    plan = moafft.Plan(list(shape), batch, -1)
+    xd = torch.from_numpy(x).cuda()
+    a = plan.exec_adjoint(xd).cpu().numpy()
+    y = plan.exec(xd)
+    z = plan.exec_adjoint(y).cpu().numpy()
+    assert plan.status() == 0
+    plan.destroy()
+    x64 = x.astype(np.complex128).reshape((batch,) + shape)
+    assert rel(a, oracle.fft_radix2(x64, 1), batch).max() <= TOL
+    n = int(np.prod(shape))
+    assert rel(z / n, x64, batch).max() <= 2 * TOL
+
+
+@pytest.mark.parametrize("v,shape,batch", [(3, (512,), 65), (3, (128,), 40), (1, (1024,), 9), (2, (4096,), 3)])
+def test_schedule_eight_byte_aligned(env, sched, v, shape, batch):
+    """Buffers one complex64 past a 16-byte boundary (the ABI asks for 8-byte
+    alignment only), out of place and in place."""
+    torch, moafft, oracle = env
+    from paper_0811_2535_gb300 import inputs
+    sched(v)
+    n = int(np.prod(shape)) * batch
+    x = inputs.uniform((batch,) + shape, 8600 + v + batch)
+    bin_ = torch.empty(n + 1, dtype=torch.complex64, device="cuda")
+    bout = torch.empty(n + 1, dtype=torch.complex64, device="cuda")
+    xin, yout = bin_[1:], bout[1:]
+    assert xin.data_ptr() % 16 == 8 and yout.data_ptr() % 16 == 8
+    xin.copy_(torch.from_numpy(x.reshape(-1)))
+    plan = moafft.Plan(list(shape), batch, -1)
+    plan.exec(xin, out=yout)
+    plan.exec(xin, out=xin)
+    assert plan.status() == 0
+    plan.destroy()
+    ref = oracle.fft_radix2(x.astype(np.complex128).reshape((batch,) + shape), -1)
+    assert rel(yout.cpu().numpy(), ref, batch).max() <= TOL
+    assert rel(xin.cpu().numpy(), ref, batch).max() <= TOL
+
+
+@pytest.mark.parametrize("v,shape,batch", [(3, (256,), 1000), (1, (1 << 19,), 2)])
+def test_schedule_cuda_graph(env, sched, v, shape, batch):
+    """Execs in schedule v captured in a CUDA graph and replayed twice give
+    the bits of the same execs run directly."""
+    torch, _, _ = env
+    from paper_0811_2535_gb300 import inputs, moafft
+    sched(v, pipe=0)
+    x = torch.from_numpy(inputs.uniform((batch,) + shape, 8700 + v)).cuda()
+    plan = moafft.Plan(list(shape), batch, -1)
+    y = torch.empty_like(x)
+    plan.exec(x, y)
+    torch.cuda.synchronize()
+    ref = y.clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plan.exec(x, y)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.exec(x, y)
+    for _ in range(2):
+        y.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(y, ref)
+    assert plan.status() == 0
+    plan.destroy()
+
+
+@pytest.mark.parametrize("v,L", [(2, 12), (1, 11), (3, 9)])
+def test_schedule_full_size_sampled(env, sched, v, L):
+    """2^24 points of rows (the size of the benchmark's transforms) in schedule
+    v: 64 sampled rows against the oracle one by one."""
+    torch, moafft, oracle = env
+    from paper_0811_2535_gb300 import inputs
+    sched(v)
+    n, batch = 1 << L, (1 << 24) >> L
+    x = inputs.uniform((batch, n), 8800 + L)
+    plan = moafft.Plan([n], batch, -1)
+    y = plan.exec(torch.from_numpy(x).cuda()).cpu().numpy().reshape(batch, n)
+    assert plan.status() == 0
+    plan.destroy()
+    rows = np.random.default_rng(L).choice(batch, 64, replace=False)
+    ref = oracle.fft_radix2(x[rows].astype(np.complex128), -1)
+    assert rel(y[rows], ref, 64).max() <= TOL
